@@ -1,0 +1,220 @@
+/*
+ * kfvm.h -- C ABI of the GB300 (sm_103a) KFVM-WENO hot path.
+ *
+ * The library computes the semi-discrete right-hand side and the SSP-RK3
+ * update of the compressible Euler equations (Eq. 1 and the Euler system of
+ * Sec. 1) with the kernel-based, fully multidimensional WENO-AO finite volume
+ * method of May & Lee, "KFVM-WENO: a high-order accurate kernel-based finite
+ * volume method for compressible hydrodynamics" (arXiv 2401.16543).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers named U, dUdt, faces are DEVICE pointers owned by the caller; the
+ * library never frees or keeps them beyond the call.  The library owns its
+ * weight tables, its scratch buffers and the gate network, all allocated by
+ * kfvm_init / kfvm_build_weights / kfvm_gate_* and released by kfvm_destroy.
+ * A `stream` argument is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream); every call is asynchronous on it unless stated otherwise.
+ *
+ * State layout: float64, structure of arrays [var][z][y][x], x fastest,
+ * interior cells only (ghost cells are never stored).  Variables are
+ * (rho, rho*u, rho*v, [rho*w,] E): nv = dims + 2.
+ *
+ * Face (Riemann) state layout: [point][var][cell] with point index
+ * s = (dir*2 + side)*R^(dims-1) + t, side 0 the low face (x_dir = -1/2),
+ * t = t0 + R*t1 over the transverse axes in increasing order and the
+ * Gauss-Legendre nodes (R per face dimension, Sec. 5.1) ascending.  In the
+ * FP64 precision mode the values are float64 conservative variables; in the
+ * FP32 mode they are float32 PRIMITIVE variables (rho, u, v, [w,] p).
+ *
+ * Errors: every call returns a kfvm_status; nothing throws across the ABI.
+ * Device-side failures (a non-admissible state, a NaN) raise a device flag
+ * that kfvm_sync_status reads (and kfvm_step reads when dt_out is given).
+ * A context is not thread-safe; use one per host thread or serialise.
+ * There is no CPU fallback: without a CUDA device every compute call returns
+ * KFVM_ERR_CUDA.
+ */
+#ifndef KFVM_H
+#define KFVM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KFVM_OK = 0,
+  KFVM_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, unsupported option) */
+  KFVM_ERR_CUDA = 2,         /* a CUDA runtime call failed (no device, launch failure)         */
+  KFVM_ERR_SINGULAR = 3,     /* a weight system could not be factored                           */
+  KFVM_ERR_NONPHYSICAL = 4,  /* rho <= 0, p <= 0 or NaN met in a cell average or Riemann state */
+  KFVM_ERR_STATE = 5,        /* call out of order (e.g. a step before kfvm_build_weights)      */
+  KFVM_ERR_TIMEOUT = 6,      /* a bounded device wait gave up                                   */
+  KFVM_ERR_NOMEM = 7         /* device or host allocation failed                                */
+} kfvm_status;
+
+typedef enum { KFVM_BC_PERIODIC = 0, KFVM_BC_OUTFLOW = 1 } kfvm_bc;
+
+/* Uniform Cartesian grid.  n[2] = 1 and lo/hi[2] unused in 2D.  bc[a][0] is
+ * the low side of axis a, bc[a][1] the high side; periodic must be set on
+ * both sides of an axis.  Ghost cells (Sec. 5.3 step 1): periodic wraps,
+ * outflow copies the nearest interior cell. */
+typedef struct {
+  int n[3];
+  double lo[3];
+  double hi[3];
+  int bc[3][2];
+} kfvm_grid;
+
+typedef struct kfvm_ctx kfvm_ctx;
+
+/* ------------------------------------------------------------------------- */
+/* Set-up (Sec. 5.1, stage (i) of the method)                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Create a context for a dims-D grid (dims = 2 or 3) with stencil radius R
+ * (2 or 3; Sec. 3.1), kernel length scale ell/Delta (the paper uses 5,
+ * Sec. 5.1) and ratio of specific heats gamma.  Enumerates S0 and its 2*dims+1
+ * substencils (Sec. 3.1), picks each polynomial degree as the largest that
+ * keeps the cell-average monomial matrix unisolvent (Sec. 2.1, exact rank over
+ * the integers mod two 61-bit primes), and allocates the device buffers.
+ * Requires an exactly uniform spacing per axis; cells may be non-square.
+ * Errors: KFVM_ERR_ARG (null out/grid, dims/R outside {2,3}, n < 1,
+ * hi <= lo, ell <= 0, gamma <= 1, mixed periodic sides), KFVM_ERR_CUDA,
+ * KFVM_ERR_NOMEM.  On error *out is NULL. */
+kfvm_status kfvm_init(kfvm_ctx** out, const kfvm_grid* grid, int dims, int radius, double ell_over_dx, double gamma);
+
+/* Build every reconstruction vector r (face Gauss points; Eqs. 14-18) and
+ * derivative vector (Eq. 23, multi-indices 0 < |alpha| <= R) of every
+ * (sub)stencil on the GPU: one CTA per (sub)stencil assembles the saddle-point
+ * system [[Q^T, P], [P^T, 0]] [r; w] = [T; S] in double-double arithmetic
+ * (kernel integrals through series for erf and exp written for this library)
+ * and solves it by Gaussian elimination with partial pivoting, then rounds to
+ * float64.  Must precede every compute call.  Synchronises the stream.
+ * Errors: KFVM_ERR_SINGULAR, KFVM_ERR_CUDA. */
+kfvm_status kfvm_build_weights(kfvm_ctx* ctx, void* stream);
+
+/* Copy the weight tables to host memory (synchronous).  Layout: for
+ * q = 0..N_S, the F x N_q face rows, then the M x N_q derivative rows.
+ * count must equal kfvm_weights_count(ctx).  Errors: KFVM_ERR_ARG,
+ * KFVM_ERR_STATE (weights not built). */
+kfvm_status kfvm_get_weights(kfvm_ctx* ctx, double* host, size_t count);
+size_t kfvm_weights_count(const kfvm_ctx* ctx);
+
+/* Options (key, value):
+ *   "precision"   64 (default) or 32: arithmetic of the reconstruction,
+ *                 Riemann solve and flux divergence.  The state and its RK
+ *                 accumulation stay float64 in both modes.
+ *   "recon"       0 WENO-AO in linearized primitive variables on every cell
+ *                 (default; Sec. 3, Sec. 5.3), 1 unlimited linear S0
+ *                 reconstruction of the conservative variables on every cell
+ *                 (Sec. 5.3 step 2a), 2 gated: cells the gate network marks
+ *                 smooth take the linear reconstruction, the others WENO-AO.
+ *   "riemann"     0 HLLC (default), 1 HLL; Batten wave speeds (Sec. 5.4).
+ *   "positivity"  1 (default) apply the positivity-preserving limiter of
+ *                 Sec. 4 to the Riemann states; 0 off.
+ *   "kappa", "eta"  bound relaxation and flattener of Sec. 4.1 (0.1, 0).
+ *   "eps"         epsilon of the nonlinear weights, Eq. 24 (1e-40).
+ *   "gate_threshold"  probability above which a cell is treated as smooth (0.5).
+ * Errors: KFVM_ERR_ARG for an unknown key or value out of range. */
+kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double value);
+
+/* ------------------------------------------------------------------------- */
+/* The hot path (Sec. 5.3, stage (iii) of the method)                         */
+/* ------------------------------------------------------------------------- */
+
+/* Riemann states at every face Gauss point of every cell (Sec. 5.3 steps 1-3):
+ * ghost-cell map, linearized primitive transform (Eq. 33, appendix A with the
+ * exact inverse), contraction with the weight tables, smoothness indicators
+ * (Eq. 22), nonlinear weights (Eqs. 24-25), WENO-AO blend (Eq. 19), back
+ * transform (Eq. 28), then the positivity limiter (Sec. 4) when enabled.
+ * U: device, float64 state.  faces: device, F*nv*ncell values in the layout
+ * and type described above.  Errors: KFVM_ERR_ARG, KFVM_ERR_STATE,
+ * KFVM_ERR_CUDA (launch); non-admissible states raise the device flag. */
+kfvm_status kfvm_reconstruct(kfvm_ctx* ctx, const double* U, void* faces, void* stream);
+
+/* Flux divergence from Riemann states (Sec. 5.3 steps 4-6): exterior states at
+ * physical boundaries (periodic: the neighbour's; outflow: a copy of the
+ * interior state), HLLC/HLL at every face Gauss point, Gauss-Legendre face
+ * average, dUdt = -sum_d (F_{d,+} - F_{d,-}) / Delta_d.
+ * faces: device, as written by kfvm_reconstruct in the same precision mode.
+ * dUdt: device, float64 [var][cell]. */
+kfvm_status kfvm_flux(kfvm_ctx* ctx, const void* faces, double* dUdt, void* stream);
+
+/* dUdt = L(U): kfvm_reconstruct followed by kfvm_flux through the library's
+ * own face buffer. */
+kfvm_status kfvm_rhs(kfvm_ctx* ctx, const double* U, double* dUdt, void* stream);
+
+/* One SSP-RK3 (Shu-Osher) step of U in place:
+ *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));  U = 1/3 U + 2/3 (U2 + dt L(U2)),
+ * with dt = cfl / max_cells sum_d (|u_d| + c)/Delta_d computed on the device
+ * from U and clipped to t_remaining.  The step never leaves the device: dt
+ * stays in device memory.  If dt_out is non-NULL the call synchronises the
+ * stream, writes dt to *dt_out and returns the device status flag.  U must
+ * not alias the library's scratch.  Errors: as kfvm_reconstruct. */
+kfvm_status kfvm_step(kfvm_ctx* ctx, double* U, double cfl, double t_remaining, double* dt_out, void* stream);
+
+/* Synchronise the stream and return (and clear) the device status flag. */
+kfvm_status kfvm_sync_status(kfvm_ctx* ctx, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Learned gate (an extension, no counterpart in the paper; it plays the role  */
+/* of the troubled-cell indicator of Sec. 3.5: cells it marks smooth skip     */
+/* WENO, exactly as the indicator's unflagged cells do, Sec. 5.3 step 2).    */
+/* ------------------------------------------------------------------------- */
+
+/* Network: in -> 32 -> 32 -> 1, ReLU hidden layers, sigmoid output; the input
+ * is the radius-2 full stencil of rho and p (cell-average pressure), each
+ * normalised by its stencil mean: 2*|S0(R=2)| values (26 in 2D, 66 in 3D).
+ * Parameters are float32 masters; inference and training run in BF16 with
+ * FP32 accumulation.  Packed parameter order: W1 [32][in], b1 [32],
+ * W2 [32][32], b2 [32], W3 [1][32], b3 [1]. */
+size_t kfvm_gate_param_count(const kfvm_ctx* ctx);
+kfvm_status kfvm_gate_set_params(kfvm_ctx* ctx, const float* host_params, size_t count);
+kfvm_status kfvm_gate_get_params(kfvm_ctx* ctx, float* host_params, size_t count);
+
+/* Gate inputs and WENO-AO training labels of every cell of U:
+ * X (device, float32 [ncell][in]) and y (device, float32 [ncell]) with
+ * y = 1 when min over the rho and p linearized-primitive components of
+ * omega_0/gamma_0 >= 1 - tau (the cell's own WENO-AO weights say it is
+ * smooth), else 0. */
+kfvm_status kfvm_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, void* stream);
+
+/* Smooth-cell probabilities prob (device, float32 [n]) for inputs X. */
+kfvm_status kfvm_gate_forward(kfvm_ctx* ctx, const float* X, float* prob, size_t n, void* stream);
+
+/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean binary
+ * cross-entropy of the batch (X, y) of n samples; the batch loss is written
+ * to *loss_dev (device float32) when non-NULL.  grads_out (device float32,
+ * kfvm_gate_param_count values) receives the batch gradient when non-NULL. */
+kfvm_status kfvm_gate_train_step(kfvm_ctx* ctx, const float* X, const float* y, size_t n, float lr,
+                                 float* loss_dev, float* grads_out, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Introspection and lifetime                                                  */
+/* ------------------------------------------------------------------------- */
+
+/* Host-only stencil description (no GPU needed): sizes[q] = N_q and
+ * degrees[q] = p_q for q = 0..N_S (arrays of at least 8), *nface = F,
+ * *nderiv = M; returns the number of (sub)stencils N_S + 1, or -1 for an
+ * unsupported (dims, radius). */
+int kfvm_stencil_info(int dims, int radius, int* sizes, int* degrees, int* nface, int* nderiv);
+
+/* Number of kernels the library launched on this context since creation
+ * (for launch accounting). */
+long long kfvm_launch_count(const kfvm_ctx* ctx);
+
+/* Measure the device's FP64 (bits = 64) or FP32 (bits = 32) FMA throughput
+ * with a register-only multiply-add loop on every SM; writes flop/s to
+ * *flops.  Synchronous. */
+kfvm_status kfvm_measure_fma_peak(int bits, double* flops);
+
+void kfvm_destroy(kfvm_ctx* ctx);
+const char* kfvm_status_string(kfvm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KFVM_H */

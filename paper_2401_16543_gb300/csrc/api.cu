@@ -1,0 +1,406 @@
+// api.cu -- the C ABI of include/kfvm.h: context lifetime, host-side set-up
+// (stencils, polynomial degrees, options) and the orchestration of the
+// device kernels for reconstruct / flux / rhs / SSP-RK3 step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace kfvm;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Polynomial degree of a (sub)stencil: the largest p whose cell-average
+// monomial matrix P is unisolvent (full column rank) over the stencil
+// (Sec. 2.1).  Column v of P scaled by prod_k 2^(a_k+1) (a_k+1) is the integer
+// prod_k [(2o_k+1)^(a_k+1) - (2o_k-1)^(a_k+1)], so the rank is exact integer
+// arithmetic; it is computed modulo two 61-bit primes (the rank over Q is at
+// least the rank mod p, and equal unless p divides every nonzero maximal
+// minor).
+// ---------------------------------------------------------------------------
+constexpr uint64_t kPrimes[2] = {2305843009213693951ULL, 4611686018427387847ULL};
+
+uint64_t mulmod(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((unsigned __int128)a * b % p); }
+
+uint64_t powmod(uint64_t a, uint64_t e, uint64_t p) {
+  uint64_t r = 1;
+  while (e) {
+    if (e & 1) r = mulmod(r, a, p);
+    a = mulmod(a, a, p);
+    e >>= 1;
+  }
+  return r;
+}
+
+int rank_mod(std::vector<std::vector<int64_t>> rows, uint64_t p) {
+  const size_t nr = rows.size(), nc = nr ? rows[0].size() : 0;
+  std::vector<std::vector<uint64_t>> m(nr, std::vector<uint64_t>(nc));
+  for (size_t i = 0; i < nr; ++i)
+    for (size_t j = 0; j < nc; ++j) {
+      int64_t v = rows[i][j] % (int64_t)p;  // both primes are below 2^63
+      m[i][j] = v < 0 ? (uint64_t)(v + (int64_t)p) : (uint64_t)v;
+    }
+  int rank = 0;
+  for (size_t c = 0; c < nc && (size_t)rank < nr; ++c) {
+    size_t piv = nr;
+    for (size_t r = rank; r < nr; ++r)
+      if (m[r][c]) { piv = r; break; }
+    if (piv == nr) continue;
+    std::swap(m[rank], m[piv]);
+    uint64_t inv = powmod(m[rank][c], p - 2, p);
+    for (size_t r = 0; r < nr; ++r) {
+      if ((int)r == rank || !m[r][c]) continue;
+      uint64_t f = mulmod(m[r][c], inv, p);
+      for (size_t j = c; j < nc; ++j) m[r][j] = (m[r][j] + p - mulmod(f, m[rank][j], p)) % p;
+    }
+    ++rank;
+  }
+  return rank;
+}
+
+int64_t ipow64(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// multi-indices with |alpha| <= p, by total degree then alpha_x descending (3 ints each)
+std::vector<int> monomials(int dim, int p, bool skip_constant) {
+  std::vector<int> out;
+  for (int n = skip_constant ? 1 : 0; n <= p; ++n) {
+    if (dim == 2) {
+      for (int a = n; a >= 0; --a) { out.push_back(a); out.push_back(n - a); out.push_back(0); }
+    } else {
+      for (int a = n; a >= 0; --a)
+        for (int b = n - a; b >= 0; --b) { out.push_back(a); out.push_back(b); out.push_back(n - a - b); }
+    }
+  }
+  return out;
+}
+
+int max_unisolvent_degree(int dim, const std::vector<int>& offs /* n x 3 */) {
+  const int n = (int)offs.size() / 3;
+  int p = 0;
+  for (;;) {
+    std::vector<int> mons = monomials(dim, p + 1, false);
+    const int D = (int)mons.size() / 3;
+    if (D > n) return p;
+    std::vector<std::vector<int64_t>> P(n, std::vector<int64_t>(D));
+    for (int h = 0; h < n; ++h)
+      for (int v = 0; v < D; ++v) {
+        int64_t e = 1;
+        for (int k = 0; k < dim; ++k) {
+          int o = offs[3 * h + k], a = mons[3 * v + k];
+          e *= ipow64(2 * o + 1, a + 1) - ipow64(2 * o - 1, a + 1);
+        }
+        P[h][v] = e;
+      }
+    int r = 0;
+    for (uint64_t pr : kPrimes) {
+      int rr = rank_mod(P, pr);
+      if (rr > r) r = rr;
+    }
+    if (r < D) return p;
+    ++p;
+  }
+}
+
+const StencilTable* table_for(int dims, int R) {
+  static const StencilTable t22 = make_stencil(2, 2), t23 = make_stencil(2, 3), t32 = make_stencil(3, 2),
+                            t33 = make_stencil(3, 3);
+  if (dims == 2 && R == 2) return &t22;
+  if (dims == 2 && R == 3) return &t23;
+  if (dims == 3 && R == 2) return &t32;
+  if (dims == 3 && R == 3) return &t33;
+  return nullptr;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+kfvm_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return KFVM_OK;
+  if (e == cudaErrorMemoryAllocation) return KFVM_ERR_NOMEM;
+  return KFVM_ERR_CUDA;
+}
+
+#define KFVM_TRY(expr)                                 \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return cuda_status(e_);     \
+  } while (0)
+
+kfvm_status check_ready(kfvm_ctx* ctx) {
+  if (!ctx) return KFVM_ERR_ARG;
+  if (!ctx->weights_built) return KFVM_ERR_STATE;
+  if (ctx->recon == 2 && !ctx->gate_loaded) return KFVM_ERR_STATE;
+  return KFVM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kfvm_stencil_info(int dims, int radius, int* sizes, int* degrees, int* nface, int* nderiv) {
+  const StencilTable* t = table_for(dims, radius);
+  if (!t) return -1;
+  for (int q = 0; q < t->nq; ++q) {
+    std::vector<int> offs;
+    for (int l = 0; l < t->len[q]; ++l)
+      for (int k = 0; k < 3; ++k) offs.push_back(t->off[t->idx[q][l]][k]);
+    if (sizes) sizes[q] = t->len[q];
+    if (degrees) degrees[q] = max_unisolvent_degree(dims, offs);
+  }
+  if (nface) *nface = 2 * dims * ipow(radius, dims - 1);
+  if (nderiv) *nderiv = n_multi(dims, radius);
+  return t->nq;
+}
+
+const char* kfvm_status_string(kfvm_status s) {
+  switch (s) {
+    case KFVM_OK: return "ok";
+    case KFVM_ERR_ARG: return "invalid argument";
+    case KFVM_ERR_CUDA: return "CUDA error";
+    case KFVM_ERR_SINGULAR: return "singular weight system";
+    case KFVM_ERR_NONPHYSICAL: return "non-admissible state (rho <= 0, p <= 0 or NaN)";
+    case KFVM_ERR_STATE: return "call out of order";
+    case KFVM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case KFVM_ERR_NOMEM: return "out of memory";
+  }
+  return "unknown status";
+}
+
+kfvm_status kfvm_init(kfvm_ctx** out, const kfvm_grid* g, int dims, int radius, double ell_over_dx, double gamma) {
+  if (!out) return KFVM_ERR_ARG;
+  *out = nullptr;
+  if (!g || (dims != 2 && dims != 3) || (radius != 2 && radius != 3)) return KFVM_ERR_ARG;
+  if (!(ell_over_dx > 0) || !(gamma > 1)) return KFVM_ERR_ARG;
+  for (int a = 0; a < dims; ++a) {
+    if (g->n[a] < 1 || !(g->hi[a] > g->lo[a])) return KFVM_ERR_ARG;
+    for (int s = 0; s < 2; ++s)
+      if (g->bc[a][s] != KFVM_BC_PERIODIC && g->bc[a][s] != KFVM_BC_OUTFLOW) return KFVM_ERR_ARG;
+    if ((g->bc[a][0] == KFVM_BC_PERIODIC) != (g->bc[a][1] == KFVM_BC_PERIODIC)) return KFVM_ERR_ARG;
+  }
+  kfvm_ctx* c = new (std::nothrow) kfvm_ctx();
+  if (!c) return KFVM_ERR_NOMEM;
+  c->dims = dims;
+  c->R = radius;
+  c->nv = dims + 2;
+  c->gamma = gamma;
+  c->ell = ell_over_dx;
+  for (int a = 0; a < 3; ++a) {
+    c->n[a] = a < dims ? g->n[a] : 1;
+    c->dx[a] = a < dims ? (g->hi[a] - g->lo[a]) / g->n[a] : 1.0;
+    for (int s = 0; s < 2; ++s) c->bc[a][s] = a < dims ? g->bc[a][s] : 0;
+  }
+  c->ncell = (long long)c->n[0] * c->n[1] * c->n[2];
+  int F = 0, M = 0;
+  c->nq = kfvm_stencil_info(dims, radius, c->sizes, c->degrees, &F, &M);
+  c->F = F;
+  c->M = M;
+  c->NT = ipow(radius, dims - 1);
+  c->n0 = c->sizes[0];
+  c->wcount = 0;
+  for (int q = 0; q < c->nq; ++q) c->wcount += (size_t)c->sizes[q] * (F + M);
+  c->gate.in = 2 * make_stencil(dims, 2).n0;
+
+  const size_t nc = (size_t)c->ncell, nv = (size_t)c->nv;
+  cudaError_t e = cudaSuccess;
+  size_t flux_total = 0;
+  for (int a = 0; a < dims; ++a) {
+    c->flux_off[a] = flux_total;
+    size_t faces = (size_t)(c->n[a] + 1) * (nc / c->n[a]);
+    flux_total += nv * faces;
+  }
+  if (e == cudaSuccess) e = dalloc(&c->d_w64, c->wcount);
+  if (e == cudaSuccess) e = dalloc(&c->d_w32, c->wcount);
+  if (e == cudaSuccess) e = dalloc((double**)&c->d_faces, (size_t)F * nv * nc);
+  if (e == cudaSuccess) e = dalloc(&c->d_flux, flux_total);
+  if (e == cudaSuccess) e = dalloc(&c->d_stage, nv * nc);
+  if (e == cudaSuccess) e = dalloc(&c->d_shadow, nv * nc);
+  if (e == cudaSuccess) e = dalloc(&c->d_gate_mask, nc);
+  if (e == cudaSuccess) e = dalloc(&c->d_scalars, 1);
+  if (e == cudaSuccess) e = dalloc(&c->d_status, 1);
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_scalars, 0, sizeof(DevScalars));
+  if (e != cudaSuccess) {
+    kfvm_destroy(c);
+    return cuda_status(e);
+  }
+  *out = c;
+  return KFVM_OK;
+}
+
+void kfvm_destroy(kfvm_ctx* c) {
+  if (!c) return;
+  cudaFree(c->d_w64);
+  cudaFree(c->d_w32);
+  cudaFree(c->d_faces);
+  cudaFree(c->d_flux);
+  cudaFree(c->d_stage);
+  cudaFree(c->d_L);
+  cudaFree(c->d_shadow);
+  cudaFree(c->d_gate_mask);
+  cudaFree(c->d_scalars);
+  cudaFree(c->d_status);
+  cudaFree(c->d_gate);
+  cudaFree(c->d_gate_adam);
+  cudaFree(c->d_gate_grad);
+  delete c;
+}
+
+size_t kfvm_weights_count(const kfvm_ctx* ctx) { return ctx ? ctx->wcount : 0; }
+
+long long kfvm_launch_count(const kfvm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+kfvm_status kfvm_build_weights(kfvm_ctx* ctx, void* stream) {
+  if (!ctx) return KFVM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d_err = nullptr;
+  KFVM_TRY(cudaMalloc(&d_err, sizeof(int)));
+  cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_build_weights(ctx, st, d_err);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (herr) return KFVM_ERR_SINGULAR;
+  ctx->w_host.assign(ctx->wcount, 0.0);
+  KFVM_TRY(cudaMemcpy(ctx->w_host.data(), ctx->d_w64, sizeof(double) * ctx->wcount, cudaMemcpyDeviceToHost));
+  std::vector<float> w32(ctx->wcount);
+  for (size_t i = 0; i < ctx->wcount; ++i) w32[i] = (float)ctx->w_host[i];
+  KFVM_TRY(cudaMemcpy(ctx->d_w32, w32.data(), sizeof(float) * ctx->wcount, cudaMemcpyHostToDevice));
+  ctx->weights_built = true;
+  return KFVM_OK;
+}
+
+kfvm_status kfvm_get_weights(kfvm_ctx* ctx, double* host, size_t count) {
+  if (!ctx || !host || count != ctx->wcount) return KFVM_ERR_ARG;
+  if (!ctx->weights_built) return KFVM_ERR_STATE;
+  std::memcpy(host, ctx->w_host.data(), sizeof(double) * count);
+  return KFVM_OK;
+}
+
+kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double v) {
+  if (!ctx || !key) return KFVM_ERR_ARG;
+  std::string k(key);
+  if (k == "precision") {
+    if (v != 64 && v != 32) return KFVM_ERR_ARG;
+    ctx->precision = (int)v;
+  } else if (k == "recon") {
+    if (v != 0 && v != 1 && v != 2) return KFVM_ERR_ARG;
+    ctx->recon = (int)v;
+  } else if (k == "riemann") {
+    if (v != 0 && v != 1) return KFVM_ERR_ARG;
+    ctx->riemann = (int)v;
+  } else if (k == "positivity") {
+    if (v != 0 && v != 1) return KFVM_ERR_ARG;
+    ctx->positivity = (int)v;
+  } else if (k == "kappa") {
+    if (!(v >= 0 && v < 1)) return KFVM_ERR_ARG;
+    ctx->kappa = v;
+  } else if (k == "eta") {
+    if (!(v >= 0 && v <= 1)) return KFVM_ERR_ARG;
+    ctx->eta = v;
+  } else if (k == "eps") {
+    if (!(v > 0)) return KFVM_ERR_ARG;
+    ctx->eps = v;
+  } else if (k == "gate_threshold") {
+    if (!(v > 0 && v < 1)) return KFVM_ERR_ARG;
+    ctx->gate_threshold = v;
+  } else {
+    return KFVM_ERR_ARG;
+  }
+  return KFVM_OK;
+}
+
+kfvm_status kfvm_reconstruct(kfvm_ctx* ctx, const double* U, void* faces, void* stream) {
+  kfvm_status s = check_ready(ctx);
+  if (s) return s;
+  if (!U || !faces) return KFVM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ctx->recon == 2) KFVM_TRY(launch_gate_mask(ctx, U, st));
+  if (ctx->precision == 64) {
+    KFVM_TRY(launch_recon64(ctx, U, (double*)faces, st));
+  } else {
+    KFVM_TRY(launch_shadow(ctx, U, ctx->d_shadow, st));
+    KFVM_TRY(launch_recon32(ctx, U, ctx->d_shadow, (float*)faces, st));
+  }
+  return KFVM_OK;
+}
+
+kfvm_status kfvm_flux(kfvm_ctx* ctx, const void* faces, double* dUdt, void* stream) {
+  kfvm_status s = check_ready(ctx);
+  if (s) return s;
+  if (!faces || !dUdt) return KFVM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  KFVM_TRY(launch_face_flux(ctx, faces, st));
+  KFVM_TRY(launch_update(ctx, 0, nullptr, nullptr, dUdt, st));
+  return KFVM_OK;
+}
+
+kfvm_status kfvm_rhs(kfvm_ctx* ctx, const double* U, double* dUdt, void* stream) {
+  kfvm_status s = kfvm_reconstruct(ctx, U, ctx ? ctx->d_faces : nullptr, stream);
+  if (s) return s;
+  return kfvm_flux(ctx, ctx->d_faces, dUdt, stream);
+}
+
+kfvm_status kfvm_step(kfvm_ctx* ctx, double* U, double cfl, double t_remaining, double* dt_out, void* stream) {
+  kfvm_status s = check_ready(ctx);
+  if (s) return s;
+  if (!U || !(cfl > 0) || !(t_remaining > 0)) return KFVM_ERR_ARG;
+  if (U == ctx->d_stage) return KFVM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool fp32 = ctx->precision == 32;
+  // dt from U (and, in the FP32 mode, the float32 shadow of U for the first stage)
+  KFVM_TRY(launch_max_rate(ctx, U, cfl, t_remaining, st));
+  const double* in[3] = {U, ctx->d_stage, ctx->d_stage};
+  double* outp[3] = {ctx->d_stage, ctx->d_stage, U};
+  for (int k = 0; k < 3; ++k) {
+    if (ctx->recon == 2) KFVM_TRY(launch_gate_mask(ctx, in[k], st));
+    if (fp32)
+      KFVM_TRY(launch_recon32(ctx, in[k], ctx->d_shadow, (float*)ctx->d_faces, st));
+    else
+      KFVM_TRY(launch_recon64(ctx, in[k], (double*)ctx->d_faces, st));
+    KFVM_TRY(launch_face_flux(ctx, ctx->d_faces, st));
+    KFVM_TRY(launch_update(ctx, k + 1, U, in[k], outp[k], st));
+  }
+  if (dt_out) {
+    KFVM_TRY(cudaMemcpyAsync(dt_out, &ctx->d_scalars->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return kfvm_sync_status(ctx, stream);
+  }
+  return KFVM_OK;
+}
+
+kfvm_status kfvm_sync_status(kfvm_ctx* ctx, void* stream) {
+  if (!ctx) return KFVM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int h = 0;
+  KFVM_TRY(cudaMemcpyAsync(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KFVM_TRY(cudaStreamSynchronize(st));
+  if (h) KFVM_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  KFVM_TRY(cudaStreamSynchronize(st));
+  if (h & kFlagNonphysical) return KFVM_ERR_NONPHYSICAL;
+  if (h & kFlagTimeout) return KFVM_ERR_TIMEOUT;
+  return KFVM_OK;
+}
+
+kfvm_status kfvm_measure_fma_peak(int bits, double* flops) {
+  if (!flops || (bits != 32 && bits != 64)) return KFVM_ERR_ARG;
+  KFVM_TRY(fma_peak(bits, flops));
+  return KFVM_OK;
+}
+
+}  // extern "C"

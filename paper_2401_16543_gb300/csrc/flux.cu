@@ -1,0 +1,528 @@
+// flux.cu -- Riemann solves, flux divergence, SSP-RK3 stage update and the
+// CFL time step (Sec. 5.3 steps 4-6, Sec. 5.4).
+//
+//   max_rate_kernel   dt = cfl / max_cells sum_d (|u_d| + c)/Delta_d clipped to
+//                     the time left: warp shuffles, one atomicMax per CTA on
+//                     the ordered bits of the (non-negative) rate, and the
+//                     last CTA to arrive (arrival counter, no waiting) writes
+//                     dt and re-arms the reduction.  In the FP32 mode it also
+//                     writes the float32 shadow of the state.
+//   face_flux_kernel  one thread per face of one direction: the Riemann states
+//                     on both sides at the R^(d-1) Gauss points (outflow:
+//                     the exterior state copies the interior one; periodic:
+//                     the wrapped neighbour), HLLC (Toro) or HLL with Batten
+//                     wave speeds (Roe-averaged u and c), Gauss-Legendre
+//                     average over the face.
+//   update_kernel     L = -sum_d (F_{d,+} - F_{d,-})/Delta_d and the Shu-Osher
+//                     stage combination in float64.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace kfvm {
+namespace {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------------------
+// CFL rate reduction and dt
+// ---------------------------------------------------------------------------
+template <int D, bool SHADOW>
+__global__ void __launch_bounds__(kBlock) max_rate_kernel(GridArgs a, const double* __restrict__ U,
+                                                          float* __restrict__ shadow, double cfl, double t_rem) {
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  const double gm1 = a.gamma - 1.0;
+  double best = 0.0;
+  for (long long c = blockIdx.x * (long long)kBlock + threadIdx.x; c < ncell; c += (long long)gridDim.x * kBlock) {
+    double u[D + 2];
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) {
+      u[v] = U[v * ncell + c];
+      if (SHADOW) shadow[v * ncell + c] = (float)u[v];
+    }
+    const double ir = 1.0 / u[0];
+    double m2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) m2 = fma(u[1 + k], u[1 + k], m2);
+    const double p = gm1 * (u[D + 1] - 0.5 * m2 * ir);
+    const double cs = sqrt(a.gamma * p * ir);
+    double rate = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) rate += (fabs(u[1 + k] * ir) + cs) / a.dx[k];
+    if (!(rate <= best)) best = rate;  // NaN propagates
+  }
+  unsigned long long bits = __double_as_longlong(best);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long ob = __shfl_down_sync(0xffffffffu, bits, o);
+    bits = ob > bits ? ob : bits;
+  }
+  __shared__ unsigned long long s_max[kBlock / 32];
+  __shared__ bool s_last;
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = bits;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = s_max[0];
+    for (int w = 1; w < kBlock / 32; ++w) m = s_max[w] > m ? s_max[w] : m;
+    atomicMax(&a.scalars->rate_bits, m);
+    __threadfence();
+    const unsigned int done = atomicAdd(&a.scalars->blocks_done, 1u);
+    s_last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long m = atomicAdd(&a.scalars->rate_bits, 0ull);
+    const double rate = __longlong_as_double((long long)m);
+    double dt = cfl / rate;
+    if (dt > t_rem) dt = t_rem;
+    if (!(rate > 0.0) || !(dt > 0.0) || !(dt <= t_rem)) {
+      raise_flag(a.status, kFlagNonphysical);
+      dt = 0.0;
+    }
+    a.scalars->dt = dt;
+    a.scalars->rate_bits = 0ull;
+    a.scalars->blocks_done = 0u;
+  }
+}
+
+__global__ void shadow_kernel(const double* __restrict__ U, float* __restrict__ S, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    S[i] = (float)U[i];
+}
+
+// ---------------------------------------------------------------------------
+// Riemann solvers
+// ---------------------------------------------------------------------------
+// Float64 states are conservative (rho, m, E); float32 states are primitive (rho, u, p).
+template <int D>
+__device__ __forceinline__ bool riemann64(const double* uL, const double* uR, int dir, double gamma, int solver,
+                                          double* f) {
+  constexpr int NV = D + 2;
+  const double gm1 = gamma - 1.0;
+  const double rL = uL[0], rR = uR[0];
+  const double irL = 1.0 / rL, irR = 1.0 / rR;
+  double vL[D], vR[D], m2L = 0.0, m2R = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    vL[k] = uL[1 + k] * irL;
+    vR[k] = uR[1 + k] * irR;
+    m2L = fma(uL[1 + k], vL[k], m2L);
+    m2R = fma(uR[1 + k], vR[k], m2R);
+  }
+  const double EL = uL[NV - 1], ER = uR[NV - 1];
+  const double pL = gm1 * (EL - 0.5 * m2L), pR = gm1 * (ER - 0.5 * m2R);
+  if (!(rL > 0.0) || !(rR > 0.0) || !(pL > 0.0) || !(pR > 0.0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = 0.0;
+    return false;
+  }
+  const double cL = sqrt(gamma * pL * irL), cR = sqrt(gamma * pR * irR);
+  const double sL = sqrt(rL), sR = sqrt(rR), isum = 1.0 / (sL + sR);
+  double ut2 = 0.0, utn = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double ut = (sL * vL[k] + sR * vR[k]) * isum;
+    ut2 = fma(ut, ut, ut2);
+    if (k == dir) utn = ut;
+  }
+  const double HL = (EL + pL) * irL, HR = (ER + pR) * irR;
+  const double Ht = (sL * HL + sR * HR) * isum;
+  const double ct2 = gm1 * (Ht - 0.5 * ut2);
+  const double ct = sqrt(ct2 > 0.0 ? ct2 : 0.0);
+  const double unL = vL[dir], unR = vR[dir];
+  const double SL = fmin(unL - cL, utn - ct), SR = fmax(unR + cR, utn + ct);
+  double FL[NV], FR[NV];
+  FL[0] = uL[1 + dir];
+  FR[0] = uR[1 + dir];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    FL[1 + k] = uL[1 + k] * unL + (k == dir ? pL : 0.0);
+    FR[1 + k] = uR[1 + k] * unR + (k == dir ? pR : 0.0);
+  }
+  FL[NV - 1] = unL * (EL + pL);
+  FR[NV - 1] = unR * (ER + pR);
+  if (SL >= 0.0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = FL[v];
+    return true;
+  }
+  if (SR <= 0.0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = FR[v];
+    return true;
+  }
+  if (solver == 1) {
+    const double idn = 1.0 / (SR - SL);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (uR[v] - uL[v])) * idn;
+    return true;
+  }
+  const double Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) / (rL * (SL - unL) - rR * (SR - unR));
+  const bool left = Ss >= 0.0;
+  const double* uK = left ? uL : uR;
+  const double* FK = left ? FL : FR;
+  const double SK = left ? SL : SR, rK = left ? rL : rR, unK = left ? unL : unR, pK = left ? pL : pR;
+  const double irK = left ? irL : irR;
+  const double fac = rK * (SK - unK) / (SK - Ss);
+  double us[NV];
+  us[0] = fac;
+#pragma unroll
+  for (int k = 0; k < D; ++k) us[1 + k] = fac * (k == dir ? Ss : uK[1 + k] * irK);
+  us[NV - 1] = fac * (uK[NV - 1] * irK + (Ss - unK) * (Ss + pK / (rK * (SK - unK))));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) f[v] = FK[v] + SK * (us[v] - uK[v]);
+  return true;
+}
+
+template <int D>
+__device__ __forceinline__ bool riemann32(const float* wL, const float* wR, int dir, float gamma, int solver,
+                                          float* f) {
+  constexpr int NV = D + 2;
+  const float gm1 = gamma - 1.0f;
+  const float rL = wL[0], rR = wR[0], pL = wL[NV - 1], pR = wR[NV - 1];
+  if (!(rL > 0.0f) || !(rR > 0.0f) || !(pL > 0.0f) || !(pR > 0.0f)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = 0.0f;
+    return false;
+  }
+  float v2L = 0.0f, v2R = 0.0f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    v2L = fmaf(wL[1 + k], wL[1 + k], v2L);
+    v2R = fmaf(wR[1 + k], wR[1 + k], v2R);
+  }
+  const float igm1 = 1.0f / gm1;
+  const float EL = fmaf(pL, igm1, 0.5f * rL * v2L), ER = fmaf(pR, igm1, 0.5f * rR * v2R);
+  const float irL = 1.0f / rL, irR = 1.0f / rR;
+  const float cL = sqrtf(gamma * pL * irL), cR = sqrtf(gamma * pR * irR);
+  const float sL = sqrtf(rL), sR = sqrtf(rR), isum = 1.0f / (sL + sR);
+  float ut2 = 0.0f, utn = 0.0f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float ut = (sL * wL[1 + k] + sR * wR[1 + k]) * isum;
+    ut2 = fmaf(ut, ut, ut2);
+    if (k == dir) utn = ut;
+  }
+  const float HL = (EL + pL) * irL, HR = (ER + pR) * irR;
+  const float Ht = (sL * HL + sR * HR) * isum;
+  const float ct2 = gm1 * (Ht - 0.5f * ut2);
+  const float ct = sqrtf(ct2 > 0.0f ? ct2 : 0.0f);
+  const float unL = wL[1 + dir], unR = wR[1 + dir];
+  const float SL = fminf(unL - cL, utn - ct), SR = fmaxf(unR + cR, utn + ct);
+  float UL[NV], UR[NV], FL[NV], FR[NV];
+  UL[0] = rL;
+  UR[0] = rR;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    UL[1 + k] = rL * wL[1 + k];
+    UR[1 + k] = rR * wR[1 + k];
+  }
+  UL[NV - 1] = EL;
+  UR[NV - 1] = ER;
+  FL[0] = UL[1 + dir];
+  FR[0] = UR[1 + dir];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    FL[1 + k] = UL[1 + k] * unL + (k == dir ? pL : 0.0f);
+    FR[1 + k] = UR[1 + k] * unR + (k == dir ? pR : 0.0f);
+  }
+  FL[NV - 1] = unL * (EL + pL);
+  FR[NV - 1] = unR * (ER + pR);
+  if (SL >= 0.0f) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = FL[v];
+    return true;
+  }
+  if (SR <= 0.0f) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = FR[v];
+    return true;
+  }
+  if (solver == 1) {
+    const float idn = 1.0f / (SR - SL);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) * idn;
+    return true;
+  }
+  const float Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) / (rL * (SL - unL) - rR * (SR - unR));
+  const bool left = Ss >= 0.0f;
+  const float* uK = left ? UL : UR;
+  const float* wK = left ? wL : wR;
+  const float* FK = left ? FL : FR;
+  const float SK = left ? SL : SR, rK = left ? rL : rR, unK = left ? unL : unR, pK = left ? pL : pR;
+  const float fac = rK * (SK - unK) / (SK - Ss);
+  float us[NV];
+  us[0] = fac;
+#pragma unroll
+  for (int k = 0; k < D; ++k) us[1 + k] = fac * (k == dir ? Ss : wK[1 + k]);
+  us[NV - 1] = fac * (uK[NV - 1] / rK + (Ss - unK) * (Ss + pK / (rK * (SK - unK))));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) f[v] = FK[v] + SK * (us[v] - uK[v]);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Face fluxes
+// ---------------------------------------------------------------------------
+struct FluxLayout {
+  long long off[3];  // start of each direction's block (in elements)
+  long long nface[3];
+};
+
+template <int D, int R, typename Real>
+__global__ void __launch_bounds__(kBlock) face_flux_kernel(GridArgs a, FluxLayout L, const Real* __restrict__ faces,
+                                                           Real* __restrict__ flux) {
+  constexpr int NV = D + 2, NT = ipow(R, D - 1);
+  const int dir = blockIdx.y;
+  const long long nf = L.nface[dir];
+  const long long f = blockIdx.x * (long long)kBlock + threadIdx.x;
+  if (f >= nf) return;
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  // face coordinates in the grid extended by one along dir
+  int e[3] = {a.n[0], a.n[1], a.n[2]};
+  e[dir] += 1;
+  long long r = f;
+  int c[3];
+  c[0] = (int)(r % e[0]);
+  r /= e[0];
+  c[1] = (int)(r % e[1]);
+  c[2] = (int)(r / e[1]);
+  const int nd = a.n[dir];
+  const int i = c[dir];
+  // cells on both sides (-1 = outside an outflow boundary)
+  int cl[3] = {c[0], c[1], c[2]}, cr[3] = {c[0], c[1], c[2]};
+  cl[dir] = i - 1;
+  cr[dir] = i;
+  bool has_l = true, has_r = true;
+  if (i == 0) {
+    if (a.bc[dir][0] == KFVM_BC_PERIODIC) cl[dir] = nd - 1; else { has_l = false; cl[dir] = 0; }
+  }
+  if (i == nd) {
+    if (a.bc[dir][1] == KFVM_BC_PERIODIC) cr[dir] = 0; else { has_r = false; cr[dir] = nd - 1; }
+  }
+  const long long lcell = ((long long)cl[2] * a.n[1] + cl[1]) * a.n[0] + cl[0];
+  const long long rcell = ((long long)cr[2] * a.n[1] + cr[1]) * a.n[0] + cr[0];
+  constexpr double w2[2] = {0.5, 0.5};
+  constexpr double w3[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  Real acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = Real(0);
+  bool ok = true;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int s_hi = (dir * 2 + 1) * NT + t, s_lo = (dir * 2) * NT + t;
+    Real uL[NV], uR[NV], fl[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const Real l = has_l ? faces[((long long)s_hi * NV + v) * ncell + lcell] : Real(0);
+      const Real rr = has_r ? faces[((long long)s_lo * NV + v) * ncell + rcell] : Real(0);
+      uL[v] = has_l ? l : rr;
+      uR[v] = has_r ? rr : l;
+    }
+    if constexpr (sizeof(Real) == 8)
+      ok &= riemann64<D>(uL, uR, dir, a.gamma, a.riemann, fl);
+    else
+      ok &= riemann32<D>(uL, uR, dir, (float)a.gamma, a.riemann, fl);
+    const double wt = (R == 2 ? w2[t % R] : w3[t % R]) * (D == 3 ? (R == 2 ? w2[t / R] : w3[t / R]) : 1.0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += Real(wt) * fl[v];
+  }
+  if (!ok) raise_flag(a.status, kFlagNonphysical);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) flux[L.off[dir] + v * nf + f] = acc[v];
+}
+
+// ---------------------------------------------------------------------------
+// Flux divergence and the SSP-RK3 stages
+// ---------------------------------------------------------------------------
+template <int D, typename Real, bool SHADOW>
+__global__ void __launch_bounds__(kBlock) update_kernel(GridArgs a, FluxLayout L, const Real* __restrict__ flux,
+                                                        int stage, const double* __restrict__ U0,
+                                                        const double* __restrict__ Us, double* __restrict__ out,
+                                                        float* __restrict__ shadow) {
+  constexpr int NV = D + 2;
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  const long long cidx = blockIdx.x * (long long)kBlock + threadIdx.x;
+  if (cidx >= ncell) return;
+  long long r = cidx;
+  int c[3];
+  c[0] = (int)(r % a.n[0]);
+  r /= a.n[0];
+  c[1] = (int)(r % a.n[1]);
+  c[2] = (int)(r / a.n[1]);
+  double Lv[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Lv[v] = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    int e[3] = {a.n[0], a.n[1], a.n[2]};
+    e[d] += 1;
+    const long long flo = ((long long)c[2] * e[1] + c[1]) * e[0] + c[0];
+    const long long stride = d == 0 ? 1 : (d == 1 ? e[0] : (long long)e[0] * e[1]);
+    const long long fhi = flo + stride;
+    const long long nf = L.nface[d];
+    const double idx = 1.0 / a.dx[d];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double lo = (double)flux[L.off[d] + v * nf + flo];
+      const double hi = (double)flux[L.off[d] + v * nf + fhi];
+      Lv[v] = fma(lo, idx, Lv[v]);
+      Lv[v] = fma(-hi, idx, Lv[v]);
+    }
+  }
+  if (stage == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * ncell + cidx] = Lv[v];
+    return;
+  }
+  const double dt = a.scalars->dt;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const long long i = v * ncell + cidx;
+    double res;
+    if (stage == 1) {
+      res = fma(dt, Lv[v], U0[i]);
+    } else if (stage == 2) {
+      res = 0.75 * U0[i] + 0.25 * fma(dt, Lv[v], Us[i]);
+    } else {
+      res = (1.0 / 3.0) * U0[i] + (2.0 / 3.0) * fma(dt, Lv[v], Us[i]);
+    }
+    out[i] = res;
+    if (SHADOW) shadow[i] = (float)res;
+  }
+}
+
+FluxLayout flux_layout(const kfvm_ctx* ctx) {
+  FluxLayout L{};
+  for (int d = 0; d < 3; ++d) {
+    L.off[d] = (long long)ctx->flux_off[d];
+    L.nface[d] = d < ctx->dims ? (long long)(ctx->n[d] + 1) * (ctx->ncell / ctx->n[d]) : 0;
+  }
+  return L;
+}
+
+template <int D, int R>
+cudaError_t face_flux_dr(kfvm_ctx* ctx, const void* faces, cudaStream_t st) {
+  const GridArgs a = make_grid_args(ctx);
+  const FluxLayout L = flux_layout(ctx);
+  long long mx = 0;
+  for (int d = 0; d < D; ++d) mx = L.nface[d] > mx ? L.nface[d] : mx;
+  dim3 grid((unsigned)((mx + kBlock - 1) / kBlock), D);
+  if (ctx->precision == 64)
+    face_flux_kernel<D, R, double><<<grid, kBlock, 0, st>>>(a, L, (const double*)faces, ctx->d_flux);
+  else
+    face_flux_kernel<D, R, float><<<grid, kBlock, 0, st>>>(a, L, (const float*)faces, (float*)ctx->d_flux);
+  ctx->launches += 1;
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t update_d(kfvm_ctx* ctx, int stage, const double* U0, const double* Us, double* out, cudaStream_t st) {
+  const GridArgs a = make_grid_args(ctx);
+  const FluxLayout L = flux_layout(ctx);
+  const unsigned blocks = (unsigned)((ctx->ncell + kBlock - 1) / kBlock);
+  const bool shadow = ctx->precision == 32 && stage >= 1 && stage <= 2;
+  if (ctx->precision == 64)
+    update_kernel<D, double, false><<<blocks, kBlock, 0, st>>>(a, L, ctx->d_flux, stage, U0, Us, out, nullptr);
+  else if (shadow)
+    update_kernel<D, float, true><<<blocks, kBlock, 0, st>>>(a, L, (const float*)ctx->d_flux, stage, U0, Us, out,
+                                                             ctx->d_shadow);
+  else
+    update_kernel<D, float, false><<<blocks, kBlock, 0, st>>>(a, L, (const float*)ctx->d_flux, stage, U0, Us, out,
+                                                              nullptr);
+  ctx->launches += 1;
+  return cudaGetLastError();
+}
+
+// register-only multiply-add loop for the FMA peak measurement
+template <typename T>
+__global__ void fma_loop(T* out, int iters, T a, T b) {
+  T x0 = threadIdx.x * (T)1e-3, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+  T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      x0 = x0 * a + b; x1 = x1 * a + b; x2 = x2 * a + b; x3 = x3 * a + b;
+      x4 = x4 * a + b; x5 = x5 * a + b; x6 = x6 * a + b; x7 = x7 * a + b;
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+template <typename T>
+cudaError_t fma_peak_t(double* flops) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int blocks = sms * 4, threads = 256, iters = sizeof(T) == 8 ? 2000 : 40000;
+  T* out = nullptr;
+  e = cudaMalloc(&out, sizeof(T) * blocks * threads);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fma_loop<T><<<blocks, threads>>>(out, iters / 10, (T)0.999, (T)0.001);
+  cudaEventRecord(e0);
+  fma_loop<T><<<blocks, threads>>>(out, iters, (T)0.999, (T)0.001);
+  cudaEventRecord(e1);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *flops = 2.0 * 8 * 16 * (double)iters * blocks * threads / (ms * 1e-3);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_max_rate(kfvm_ctx* ctx, const double* U, double cfl, double t_rem, cudaStream_t st) {
+  const GridArgs a = make_grid_args(ctx);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long want = (ctx->ncell + kBlock - 1) / kBlock;
+  unsigned blocks = (unsigned)(want < 8LL * sms ? want : 8LL * sms);
+  if (blocks == 0) blocks = 1;
+  const bool sh = ctx->precision == 32;
+  if (ctx->dims == 2) {
+    if (sh) max_rate_kernel<2, true><<<blocks, kBlock, 0, st>>>(a, U, ctx->d_shadow, cfl, t_rem);
+    else max_rate_kernel<2, false><<<blocks, kBlock, 0, st>>>(a, U, nullptr, cfl, t_rem);
+  } else {
+    if (sh) max_rate_kernel<3, true><<<blocks, kBlock, 0, st>>>(a, U, ctx->d_shadow, cfl, t_rem);
+    else max_rate_kernel<3, false><<<blocks, kBlock, 0, st>>>(a, U, nullptr, cfl, t_rem);
+  }
+  ctx->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shadow(kfvm_ctx* ctx, const double* U, float* shadow, cudaStream_t st) {
+  const long long n = ctx->ncell * ctx->nv;
+  unsigned blocks = (unsigned)((n + kBlock - 1) / kBlock);
+  if (blocks > 65535u * 8u) blocks = 65535u * 8u;
+  shadow_kernel<<<blocks, kBlock, 0, st>>>(U, shadow, n);
+  ctx->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_flux(kfvm_ctx* ctx, const void* faces, cudaStream_t st) {
+  if (ctx->dims == 2 && ctx->R == 2) return face_flux_dr<2, 2>(ctx, faces, st);
+  if (ctx->dims == 2 && ctx->R == 3) return face_flux_dr<2, 3>(ctx, faces, st);
+  if (ctx->dims == 3 && ctx->R == 2) return face_flux_dr<3, 2>(ctx, faces, st);
+  return face_flux_dr<3, 3>(ctx, faces, st);
+}
+
+cudaError_t launch_update(kfvm_ctx* ctx, int stage, const double* U0, const double* Us, double* out,
+                          cudaStream_t st) {
+  if (ctx->dims == 2) return update_d<2>(ctx, stage, U0, Us, out, st);
+  return update_d<3>(ctx, stage, U0, Us, out, st);
+}
+
+cudaError_t fma_peak(int bits, double* flops) {
+  return bits == 64 ? fma_peak_t<double>(flops) : fma_peak_t<float>(flops);
+}
+
+}  // namespace kfvm

@@ -1,0 +1,94 @@
+// internal.h -- context and launch interfaces shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <vector>
+
+#include "../../include/kfvm.h"
+#include "geometry.h"
+
+namespace kfvm {
+
+// Device-side status bits (OR-ed into ctx->d_status).
+enum : int { kFlagNonphysical = 1, kFlagTimeout = 2 };
+
+// Scalars the kernels exchange through device memory.
+struct DevScalars {
+  unsigned long long rate_bits;  // max over cells of sum_d (|u_d| + c)/dx_d, as ordered bits
+  unsigned int blocks_done;      // arrival counter of the reduction's last-block pattern
+  unsigned int pad;
+  double dt;                     // current step size
+  double cfl, t_rem;             // inputs of the dt rule
+};
+
+struct GateNet {
+  int in = 0;
+  static constexpr int H = 32;
+  size_t count() const { return (size_t)H * in + H + H * H + H + H + 1; }
+};
+
+}  // namespace kfvm
+
+struct kfvm_ctx {
+  // geometry and physics
+  int dims = 2, R = 2, nv = 4, nq = 6, n0 = 13, F = 8, M = 5, NT = 2;
+  int n[3] = {1, 1, 1};
+  double dx[3] = {1, 1, 1};
+  int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  double gamma = 1.4, ell = 5.0;
+  long long ncell = 0;
+  int sizes[kfvm::kMaxNQ] = {0};
+  int degrees[kfvm::kMaxNQ] = {0};
+  // options
+  int precision = 64, recon = 0, riemann = 0, positivity = 1;
+  double kappa = 0.1, eta = 0.0, eps = 1e-40, gate_threshold = 0.5;
+  // weights
+  size_t wcount = 0;
+  bool weights_built = false;
+  std::vector<double> w_host;  // float64 tables (kernel-parameter copies are made from these)
+  double* d_w64 = nullptr;
+  float* d_w32 = nullptr;
+  // scratch owned by the library
+  void* d_faces = nullptr;       // F * nv * ncell values (float64 or float32)
+  double* d_flux = nullptr;      // face-averaged fluxes, per direction nv * (n_d + 1) * prod(n_other)
+  size_t flux_off[3] = {0, 0, 0};
+  double* d_stage = nullptr;     // one intermediate RK state, nv * ncell
+  double* d_L = nullptr;         // optional dUdt scratch for kfvm_rhs-style calls
+  float* d_shadow = nullptr;     // float32 copy of the state for the FP32 path, nv * ncell
+  unsigned char* d_gate_mask = nullptr;  // per cell: 1 = smooth (linear), 0 = WENO
+  kfvm::DevScalars* d_scalars = nullptr;
+  int* d_status = nullptr;
+  // gate
+  kfvm::GateNet gate;
+  float* d_gate = nullptr;        // float32 master parameters
+  float* d_gate_adam = nullptr;   // Adam moments m, v (2 * count)
+  float* d_gate_grad = nullptr;   // gradient accumulator
+  long long gate_step = 0;
+  bool gate_loaded = false;
+  // accounting
+  long long launches = 0;
+};
+
+namespace kfvm {
+
+// Launch helpers implemented per translation unit.  Every launcher returns a
+// cudaError_t from cudaGetLastError() after its launches and adds the number
+// of kernels it launched to ctx->launches.
+cudaError_t launch_build_weights(kfvm_ctx* ctx, cudaStream_t st, int* d_err);
+cudaError_t launch_max_rate(kfvm_ctx* ctx, const double* U, double cfl, double t_rem, cudaStream_t st);
+cudaError_t launch_recon64(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_t st);
+cudaError_t launch_recon32(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st);
+cudaError_t launch_face_flux(kfvm_ctx* ctx, const void* faces, cudaStream_t st);
+// stage: 0 -> dUdt only (to out), 1/2/3 -> SSP-RK3 stages writing the new state to out.
+cudaError_t launch_update(kfvm_ctx* ctx, int stage, const double* U0, const double* Us, double* out, cudaStream_t st);
+cudaError_t launch_shadow(kfvm_ctx* ctx, const double* U, float* shadow, cudaStream_t st);
+cudaError_t launch_gate_mask(kfvm_ctx* ctx, const double* U, cudaStream_t st);
+cudaError_t launch_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, cudaStream_t st);
+cudaError_t launch_gate_forward(kfvm_ctx* ctx, const float* X, float* prob, size_t n, cudaStream_t st);
+cudaError_t launch_gate_train(kfvm_ctx* ctx, const float* X, const float* y, size_t n, float lr, float* loss,
+                              float* grads_out, cudaStream_t st);
+cudaError_t fma_peak(int bits, double* flops);
+
+}  // namespace kfvm

@@ -1,0 +1,9 @@
+// recon64_32.cu -- FP64 Riemann states for d = 3, R = 2 (one instantiation per
+// translation unit so that the library compiles in parallel).
+#include "recon64.cuh"
+
+namespace kfvm {
+cudaError_t launch_recon64_32(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_t st) {
+  return r64::launch_dr<3, 2>(ctx, U, faces, st);
+}
+}  // namespace kfvm
