@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput of the KFVM-WENO hot path on one GB300 (or N replicas under torchrun).
+
+Metric: cell-updates/s per RK stage (cells x RK stages / time) of SSP-RK3 steps of
+the 2D Euler workload on 1024 x 1024 cells: radius-2 KFVM-WENO-AO, HLLC, the
+positivity limiter, outflow boundaries, 64 seeded Voronoi regions with
+rho, p ~ U[0.1, 1] and u, v ~ U[-1, 1] (seed 2), CFL 0.4.
+
+One printed JSON line (rank 0).  A "step" is one SSP-RK3 step: the CFL
+reduction and three RK stages (Riemann states, face fluxes, update), all in the
+library's kernels.  ``value`` is the headline path with inputs resident in
+HBM; ``fp64_plain`` is the plain FP64 GPU path on the same workload; ``e2e``
+is the headline path through the C ABI with the state copied host->device
+before and device->host after every step; ``cpu_baseline`` is the oracle on
+the host cores.  ``--impl reference`` times the oracle instead (the reference
+arm of this repository).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 1024
+RADIUS = 2
+CFL = 0.4
+METRIC = "cell-updates/s per RK stage"
+WORKLOAD = ("2D Euler 1024x1024, radius-2 KFVM-WENO-AO (linearized primitive variables), HLLC + Batten, "
+            "positivity limiter, outflow, 64 seeded Voronoi regions (rho,p~U[0.1,1], u,v~U[-1,1], seed 2), "
+            "SSP-RK3 at CFL 0.4")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", choices=["auto", "fp64", "fp32", "gated"], default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import workloads
+    crop = 128
+    U = np.ascontiguousarray(workloads.voronoi_2d(N_GRID, k=64, seed=2).numpy()[:, :crop, :crop])
+    o = oracle.Oracle([crop, crop], dim=2, R=RADIUS, bc="outflow")
+    for _ in range(args.warmup):
+        o.step(U, CFL)
+    t0 = time.perf_counter()
+    Ur = U
+    for _ in range(args.steps):
+        Ur, _ = o.step(Ur, CFL)
+    el = time.perf_counter() - t0
+    value = crop * crop * 3 * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "radius": RADIUS,
+                   "sample": f"{crop}x{crop} corner crop of the workload per step"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"SSP-RK3 steps of a {crop}x{crop} crop, single-threaded C oracle"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the GPU is loaded."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algo_flops_per_cell(dims, R, mode):
+    """Algorithmic flops of the Riemann-state kernel per cell (FMA = 2): every contraction
+    r_q(s).g_q and d_q(alpha).g_q (Eqs. 18, 22), the beta sums and the WENO-AO blend
+    (Eq. 19), for every reconstruction variable; linear mode: r_0(s).g_0 only."""
+    from paper_2401_16543_gb300 import stencil_info
+    sizes, _, F, M = stencil_info(dims, R)
+    nv, nq = dims + 2, len(sizes)
+    if mode == "linear":
+        return 2 * nv * sizes[0] * F
+    return 2 * nv * (sum(n * (F + M) for n in sizes) + nq * M + nq * F)
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+def time_steps(g, U, steps, stream, flush_buf):
+    """Per-step CUDA events on the launching stream; L2 flushed between steps (outside the events)."""
+    import torch
+    total = 0.0
+    for _ in range(steps):
+        flush_l2(flush_buf)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(U, CFL, sync=False, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total  # ms
+
+
+def make_solver(path, U_dev):
+    from paper_2401_16543_gb300 import KFVM
+    g = KFVM([N_GRID, N_GRID], dims=2, radius=RADIUS, bc="outflow")
+    if path in ("fp32", "gated"):
+        g.set_option("precision", 32)
+    if path == "gated":
+        g.set_option("recon", 2)
+    return g
+
+
+def measure_path(path, U0, steps, warmup, stream, flush_buf, profile_kernel):
+    import torch
+    g = make_solver(path, U0)
+    U = U0.clone()
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            g.step(U, CFL, sync=False, stream=stream)
+        g.sync_status(stream)
+        U.copy_(U0)
+        torch.cuda.synchronize()
+        launches0 = g.launches
+        g.set_option("profile", 1)
+        g.profile_reset()
+        ms = time_steps(g, U, steps, stream, flush_buf)
+        torch.cuda.synchronize()
+        prof = g.profile()
+        g.set_option("profile", 0)
+        launches = g.launches - launches0
+        g.sync_status(stream)
+    return g, ms, prof, launches
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2401_16543_gb300 as pkg
+    import workloads
+    pkg.load()
+    dev = torch.device("cuda", local)
+    U0 = workloads.voronoi_2d(N_GRID, k=64, seed=2, device=dev).contiguous()
+    ncell = N_GRID * N_GRID
+    stream = torch.cuda.Stream(device=dev)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    path = args.path
+    if path == "auto":
+        path = "fp64"
+    sampler = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    sampler.start()
+    # ---- headline path, resident inputs ----
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    g, ms, prof, launches = measure_path(path, U0, args.steps, args.warmup, stream, flush_buf, None)
+    torch.cuda.synchronize()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clocks = sampler.stop()
+    value = world * ncell * 3 * args.steps / (ms * 1e-3)
+
+    # ---- plain FP64 path on the same workload ----
+    if path == "fp64":
+        fp64 = {"value": value, "ms_per_step": ms / args.steps}
+    else:
+        _, ms64, _, _ = measure_path("fp64", U0, max(3, args.steps // 4), 2, stream, flush_buf, None)
+        fp64 = {"value": world * ncell * 3 * max(3, args.steps // 4) / (ms64 * 1e-3),
+                "ms_per_step": ms64 / max(3, args.steps // 4)}
+
+    # ---- end to end through the C ABI with host buffers ----
+    Uh = U0.cpu().pin_memory()
+    Uo = torch.empty_like(Uh).pin_memory()
+    U = torch.empty_like(U0)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            U.copy_(Uh, non_blocking=True)
+            g.step(U, CFL, sync=False, stream=stream)
+            Uo.copy_(U, non_blocking=True)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            U.copy_(Uh, non_blocking=True)
+            g.step(U, CFL, sync=False, stream=stream)
+            Uo.copy_(U, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms_e2e = e0.elapsed_time(e1)
+    g.sync_status(stream)
+    e2e = {"value": world * ncell * 3 * args.steps / (ms_e2e * 1e-3), "unit": "cell-updates/s",
+           "h2d_bytes_per_step": Uh.numel() * 8, "d2h_bytes_per_step": Uo.numel() * 8}
+
+    # ---- roofline of the dominant kernel ----
+    kern = "recon64" if path == "fp64" else "recon32"
+    n_launch, kms = prof.get(kern, (0, 0.0))
+    mode = "weno" if path in ("fp64", "fp32") else "gated"
+    flops = algo_flops_per_cell(2, RADIUS, "weno") * ncell
+    peak_flops = pkg.measure_fma_peak(64 if path == "fp64" else 32)
+    achieved = flops / (kms / n_launch * 1e-3) if n_launch else 0.0
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"{kern}_traffic.txt")
+    if os.path.exists(tfile):
+        for line in open(tfile):
+            if line.startswith("traffic_bytes_per_launch"):
+                traffic = float(line.split("=")[1])
+    total_prof = sum(v[1] for v in prof.values())
+    roofline = {"bound": "alu", "kernel": kern, "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak_flops if peak_flops else None, "traffic": traffic,
+                "peak_source": f"measured live: FP{64 if path == 'fp64' else 32} FMA loop on every SM",
+                "algo_flops_per_cell": flops / ncell, "mode": mode,
+                "kernel_share": {k: round(v[1] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
+
+    # ---- the oracle on the host cores ----
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import numpy as np
+
+        import oracle
+        Un = U0.cpu().numpy()
+        o = oracle.Oracle([N_GRID, N_GRID], dim=2, R=RADIUS, bc="outflow")
+        t0 = time.perf_counter()
+        o.step(Un, CFL)
+        el = time.perf_counter() - t0
+        cpu = {"value": ncell * 3 / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": "one SSP-RK3 step (3 RK stages) of the full 1024x1024 workload, single-threaded C oracle"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "gated": "f32+bf16"}[path],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "radius": RADIUS, "path": path,
+                       "l2": "flushed between timed steps (256 MB write outside the step events)",
+                       "replicas": world},
+            "fp64_plain": fp64,
+            "speedup_vs_fp64": value / fp64["value"],
+            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
+            "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()}, "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

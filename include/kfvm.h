@@ -117,6 +117,8 @@ size_t kfvm_weights_count(const kfvm_ctx* ctx);
  *   "kappa", "eta"  bound relaxation and flattener of Sec. 4.1 (0.1, 0).
  *   "eps"         epsilon of the nonlinear weights, Eq. 24 (1e-40).
  *   "gate_threshold"  probability above which a cell is treated as smooth (0.5).
+ *   "profile"     1: time every hot-path launch with CUDA events (see
+ *                 kfvm_profile_get); 0 (default) off.
  * Errors: KFVM_ERR_ARG for an unknown key or value out of range. */
 kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double value);
 
@@ -204,6 +206,17 @@ int kfvm_stencil_info(int dims, int radius, int* sizes, int* degrees, int* nface
 /* Number of kernels the library launched on this context since creation
  * (for launch accounting). */
 long long kfvm_launch_count(const kfvm_ctx* ctx);
+
+/* Per-kernel device timing (tracing).  With the option "profile" = 1 every
+ * hot-path launch is bracketed by CUDA events on its stream.  After the
+ * caller has synchronised that stream, kfvm_profile_get(ctx, i, ...) returns
+ * for kernel family i (0 <= i < kfvm_profile_count()) its name, the number of
+ * launches and their summed device time in milliseconds since the last
+ * kfvm_profile_reset.  Errors: KFVM_ERR_ARG (bad index), KFVM_ERR_CUDA (an
+ * event not yet complete: synchronise first). */
+int kfvm_profile_count(void);
+kfvm_status kfvm_profile_get(kfvm_ctx* ctx, int index, const char** name, long long* launches, double* ms);
+kfvm_status kfvm_profile_reset(kfvm_ctx* ctx);
 
 /* Measure the device's FP64 (bits = 64) or FP32 (bits = 32) FMA throughput
  * with a register-only multiply-add loop on every SM; writes flop/s to

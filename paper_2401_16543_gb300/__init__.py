@@ -70,6 +70,10 @@ def load():
     L.kfvm_launch_count.argtypes = [P]
     L.kfvm_launch_count.restype = ctypes.c_longlong
     L.kfvm_measure_fma_peak.argtypes = [I, ctypes.POINTER(D)]
+    L.kfvm_profile_count.argtypes = []
+    L.kfvm_profile_get.argtypes = [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(D)]
+    L.kfvm_profile_reset.argtypes = [P]
     L.kfvm_destroy.argtypes = [P]
     L.kfvm_destroy.restype = None
     L.kfvm_status_string.argtypes = [I]
@@ -231,6 +235,22 @@ class KFVM:
     @property
     def launches(self) -> int:
         return int(self._L.kfvm_launch_count(self._ctx))
+
+    def profile(self):
+        """{kernel family: (launches, device ms)} since the last reset (needs the "profile" option and a sync)."""
+        out = {}
+        for i in range(self._L.kfvm_profile_count()):
+            name = ctypes.c_char_p()
+            n = ctypes.c_longlong()
+            ms = ctypes.c_double()
+            _check(self._L.kfvm_profile_get(self._ctx, i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms)),
+                   "kfvm_profile_get")
+            if n.value:
+                out[name.value.decode()] = (int(n.value), float(ms.value))
+        return out
+
+    def profile_reset(self):
+        _check(self._L.kfvm_profile_reset(self._ctx), "kfvm_profile_reset")
 
     # -- learned gate --------------------------------------------------------------
     @property

@@ -141,6 +141,47 @@ kfvm_status cuda_status(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_status(e_);     \
   } while (0)
 
+cudaEvent_t pool_event(kfvm_ctx* c) {
+  if (!c->prof_free.empty()) {
+    cudaEvent_t e = c->prof_free.back();
+    c->prof_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Fold completed event pairs into the per-kernel totals; returns false if one is still pending.
+bool prof_fold(kfvm_ctx* c) {
+  bool all = true;
+  std::vector<ProfPair> keep;
+  for (const ProfPair& p : c->prof_pairs) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
+      c->prof_ms[p.kernel] += ms;
+      c->prof_launches[p.kernel] += 1;
+      c->prof_free.push_back(p.start);
+      c->prof_free.push_back(p.stop);
+    } else {
+      (void)cudaGetLastError();
+      keep.push_back(p);
+      all = false;
+    }
+  }
+  c->prof_pairs.swap(keep);
+  return all;
+}
+
+// A launcher call bracketed by tracing events.
+#define KFVM_LAUNCH(ctx, kernel, st, call)             \
+  do {                                                 \
+    cudaEvent_t ev_ = prof_begin((ctx), (st));         \
+    cudaError_t e_ = (call);                           \
+    prof_end((ctx), (kernel), ev_, (st));              \
+    if (e_ != cudaSuccess) return cuda_status(e_);     \
+  } while (0)
+
 kfvm_status check_ready(kfvm_ctx* ctx) {
   if (!ctx) return KFVM_ERR_ARG;
   if (!ctx->weights_built) return KFVM_ERR_STATE;
@@ -149,6 +190,25 @@ kfvm_status check_ready(kfvm_ctx* ctx) {
 }
 
 }  // namespace
+
+namespace kfvm {
+
+cudaEvent_t prof_begin(kfvm_ctx* ctx, cudaStream_t st) {
+  if (!ctx->profile) return nullptr;
+  cudaEvent_t e = pool_event(ctx);
+  if (e) cudaEventRecord(e, st);
+  return e;
+}
+
+void prof_end(kfvm_ctx* ctx, int kernel, cudaEvent_t start, cudaStream_t st) {
+  if (!ctx->profile || !start) return;
+  cudaEvent_t e = pool_event(ctx);
+  if (!e) return;
+  cudaEventRecord(e, st);
+  ctx->prof_pairs.push_back(ProfPair{start, e, kernel});
+}
+
+}  // namespace kfvm
 
 extern "C" {
 
@@ -244,6 +304,11 @@ kfvm_status kfvm_init(kfvm_ctx** out, const kfvm_grid* g, int dims, int radius, 
 
 void kfvm_destroy(kfvm_ctx* c) {
   if (!c) return;
+  for (const ProfPair& p : c->prof_pairs) {
+    cudaEventDestroy(p.start);
+    cudaEventDestroy(p.stop);
+  }
+  for (cudaEvent_t e : c->prof_free) cudaEventDestroy(e);
   cudaFree(c->d_w64);
   cudaFree(c->d_w32);
   cudaFree(c->d_faces);
@@ -317,6 +382,9 @@ kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double v) {
   } else if (k == "eps") {
     if (!(v > 0)) return KFVM_ERR_ARG;
     ctx->eps = v;
+  } else if (k == "profile") {
+    if (v != 0 && v != 1) return KFVM_ERR_ARG;
+    ctx->profile = (int)v;
   } else if (k == "gate_threshold") {
     if (!(v > 0 && v < 1)) return KFVM_ERR_ARG;
     ctx->gate_threshold = v;
@@ -331,12 +399,12 @@ kfvm_status kfvm_reconstruct(kfvm_ctx* ctx, const double* U, void* faces, void* 
   if (s) return s;
   if (!U || !faces) return KFVM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  if (ctx->recon == 2) KFVM_TRY(launch_gate_mask(ctx, U, st));
+  if (ctx->recon == 2) KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, U, st));
   if (ctx->precision == 64) {
-    KFVM_TRY(launch_recon64(ctx, U, (double*)faces, st));
+    KFVM_LAUNCH(ctx, kProfRecon64, st, launch_recon64(ctx, U, (double*)faces, st));
   } else {
-    KFVM_TRY(launch_shadow(ctx, U, ctx->d_shadow, st));
-    KFVM_TRY(launch_recon32(ctx, U, ctx->d_shadow, (float*)faces, st));
+    KFVM_LAUNCH(ctx, kProfShadow, st, launch_shadow(ctx, U, ctx->d_shadow, st));
+    KFVM_LAUNCH(ctx, kProfRecon32, st, launch_recon32(ctx, U, ctx->d_shadow, (float*)faces, st));
   }
   return KFVM_OK;
 }
@@ -346,8 +414,8 @@ kfvm_status kfvm_flux(kfvm_ctx* ctx, const void* faces, double* dUdt, void* stre
   if (s) return s;
   if (!faces || !dUdt) return KFVM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  KFVM_TRY(launch_face_flux(ctx, faces, st));
-  KFVM_TRY(launch_update(ctx, 0, nullptr, nullptr, dUdt, st));
+  KFVM_LAUNCH(ctx, kProfFaceFlux, st, launch_face_flux(ctx, faces, st));
+  KFVM_LAUNCH(ctx, kProfUpdate, st, launch_update(ctx, 0, nullptr, nullptr, dUdt, st));
   return KFVM_OK;
 }
 
@@ -365,17 +433,17 @@ kfvm_status kfvm_step(kfvm_ctx* ctx, double* U, double cfl, double t_remaining, 
   cudaStream_t st = (cudaStream_t)stream;
   const bool fp32 = ctx->precision == 32;
   // dt from U (and, in the FP32 mode, the float32 shadow of U for the first stage)
-  KFVM_TRY(launch_max_rate(ctx, U, cfl, t_remaining, st));
+  KFVM_LAUNCH(ctx, kProfMaxRate, st, launch_max_rate(ctx, U, cfl, t_remaining, st));
   const double* in[3] = {U, ctx->d_stage, ctx->d_stage};
   double* outp[3] = {ctx->d_stage, ctx->d_stage, U};
   for (int k = 0; k < 3; ++k) {
-    if (ctx->recon == 2) KFVM_TRY(launch_gate_mask(ctx, in[k], st));
+    if (ctx->recon == 2) KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, in[k], st));
     if (fp32)
-      KFVM_TRY(launch_recon32(ctx, in[k], ctx->d_shadow, (float*)ctx->d_faces, st));
+      KFVM_LAUNCH(ctx, kProfRecon32, st, launch_recon32(ctx, in[k], ctx->d_shadow, (float*)ctx->d_faces, st));
     else
-      KFVM_TRY(launch_recon64(ctx, in[k], (double*)ctx->d_faces, st));
-    KFVM_TRY(launch_face_flux(ctx, ctx->d_faces, st));
-    KFVM_TRY(launch_update(ctx, k + 1, U, in[k], outp[k], st));
+      KFVM_LAUNCH(ctx, kProfRecon64, st, launch_recon64(ctx, in[k], (double*)ctx->d_faces, st));
+    KFVM_LAUNCH(ctx, kProfFaceFlux, st, launch_face_flux(ctx, ctx->d_faces, st));
+    KFVM_LAUNCH(ctx, kProfUpdate, st, launch_update(ctx, k + 1, U, in[k], outp[k], st));
   }
   if (dt_out) {
     KFVM_TRY(cudaMemcpyAsync(dt_out, &ctx->d_scalars->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -394,6 +462,34 @@ kfvm_status kfvm_sync_status(kfvm_ctx* ctx, void* stream) {
   KFVM_TRY(cudaStreamSynchronize(st));
   if (h & kFlagNonphysical) return KFVM_ERR_NONPHYSICAL;
   if (h & kFlagTimeout) return KFVM_ERR_TIMEOUT;
+  return KFVM_OK;
+}
+
+int kfvm_profile_count(void) { return kProfCount; }
+
+kfvm_status kfvm_profile_get(kfvm_ctx* ctx, int index, const char** name, long long* launches, double* ms) {
+  static const char* names[kProfCount] = {"max_rate", "recon64", "recon32", "face_flux", "update", "gate_mask",
+                                          "shadow"};
+  if (!ctx || index < 0 || index >= kProfCount) return KFVM_ERR_ARG;
+  const bool done = prof_fold(ctx);
+  if (name) *name = names[index];
+  if (launches) *launches = ctx->prof_launches[index];
+  if (ms) *ms = ctx->prof_ms[index];
+  return done ? KFVM_OK : KFVM_ERR_CUDA;
+}
+
+kfvm_status kfvm_profile_reset(kfvm_ctx* ctx) {
+  if (!ctx) return KFVM_ERR_ARG;
+  prof_fold(ctx);
+  for (const ProfPair& p : ctx->prof_pairs) {
+    ctx->prof_free.push_back(p.start);
+    ctx->prof_free.push_back(p.stop);
+  }
+  ctx->prof_pairs.clear();
+  for (int i = 0; i < kProfCount; ++i) {
+    ctx->prof_launches[i] = 0;
+    ctx->prof_ms[i] = 0.0;
+  }
   return KFVM_OK;
 }
 

@@ -23,6 +23,15 @@ struct DevScalars {
   double cfl, t_rem;             // inputs of the dt rule
 };
 
+// Kernel families timed by the "profile" option.
+enum ProfKernel : int { kProfMaxRate = 0, kProfRecon64, kProfRecon32, kProfFaceFlux, kProfUpdate, kProfGateMask,
+                        kProfShadow, kProfCount };
+
+struct ProfPair {
+  cudaEvent_t start, stop;
+  int kernel;
+};
+
 struct GateNet {
   int in = 0;
   static constexpr int H = 32;
@@ -67,8 +76,13 @@ struct kfvm_ctx {
   float* d_gate_grad = nullptr;   // gradient accumulator
   long long gate_step = 0;
   bool gate_loaded = false;
-  // accounting
+  // accounting and tracing
   long long launches = 0;
+  int profile = 0;
+  std::vector<kfvm::ProfPair> prof_pairs;   // recorded, not yet folded into the totals
+  std::vector<cudaEvent_t> prof_free;       // event pool
+  long long prof_launches[kfvm::kProfCount] = {0};
+  double prof_ms[kfvm::kProfCount] = {0};
 };
 
 namespace kfvm {
@@ -90,5 +104,9 @@ cudaError_t launch_gate_forward(kfvm_ctx* ctx, const float* X, float* prob, size
 cudaError_t launch_gate_train(kfvm_ctx* ctx, const float* X, const float* y, size_t n, float lr, float* loss,
                               float* grads_out, cudaStream_t st);
 cudaError_t fma_peak(int bits, double* flops);
+
+// Tracing helpers (no-ops unless ctx->profile): bracket one launcher call.
+cudaEvent_t prof_begin(kfvm_ctx* ctx, cudaStream_t st);
+void prof_end(kfvm_ctx* ctx, int kernel, cudaEvent_t start, cudaStream_t st);
 
 }  // namespace kfvm
