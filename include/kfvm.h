@@ -51,7 +51,8 @@ typedef enum {
   KFVM_ERR_NONPHYSICAL = 4,  /* rho <= 0, p <= 0 or NaN met in a cell average or Riemann state */
   KFVM_ERR_STATE = 5,        /* call out of order (e.g. a step before kfvm_build_weights)      */
   KFVM_ERR_TIMEOUT = 6,      /* a bounded device wait gave up                                   */
-  KFVM_ERR_NOMEM = 7         /* device or host allocation failed                                */
+  KFVM_ERR_NOMEM = 7,        /* device or host allocation failed                                */
+  KFVM_ERR_TOO_LARGE = 8     /* the problem exceeds a fixed-size buffer (kfvm_flux_static)      */
 } kfvm_status;
 
 typedef enum { KFVM_BC_PERIODIC = 0, KFVM_BC_OUTFLOW = 1 } kfvm_bc;
@@ -143,6 +144,34 @@ kfvm_status kfvm_reconstruct(kfvm_ctx* ctx, const double* U, void* faces, void* 
  * faces: device, as written by kfvm_reconstruct in the same precision mode.
  * dUdt: device, float64 [var][cell]. */
 kfvm_status kfvm_flux(kfvm_ctx* ctx, const void* faces, double* dUdt, void* stream);
+
+/* Allocation-free variant of kfvm_flux, for callers that must not allocate
+ * device memory at all: plug-ins whose host application owns the whole
+ * device-memory budget through its own pool, and latency-sensitive loops in
+ * which cudaMalloc / cudaFree (which may synchronise the device) are not
+ * allowed.  It needs no context: the caller passes the grid, dims (2 or 3),
+ * radius (2 or 3), gamma, the Riemann solver (0 HLLC, 1 HLL), float64
+ * conservative Riemann states `faces` (device, the layout of kfvm_reconstruct
+ * in the FP64 mode) and the output dUdt (device, float64 [var][cell]).  The
+ * paper has no counterpart of this entry point.
+ *
+ * Scratch: the face-averaged fluxes live in one fixed device array of
+ * 16 MiB (plus a 256-byte status word) that every GPU loading the library
+ * holds until the process exits.  Problems whose fluxes need more,
+ * (dims+2) * sum_d (n_d+1) * prod_{e != d} n_e * 8 bytes > 16 MiB
+ * (in 2D about 510 x 510 cells, in 3D about 96^3), are rejected with
+ * KFVM_ERR_TOO_LARGE before any device work.  Nothing is allocated: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  The first call
+ * made with a given device current looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call shares the one array and overwrites it, so
+ * calls that overlap on the GPU (on different streams, or from different
+ * threads) race and must be serialised by the caller.  The status word is
+ * cleared at the start of each call; if status_out (device int*) is non-NULL
+ * it receives the call's device status bits (1 = non-admissible state).
+ * Errors: KFVM_ERR_ARG, KFVM_ERR_TOO_LARGE, KFVM_ERR_CUDA. */
+kfvm_status kfvm_flux_static(const kfvm_grid* grid, int dims, int radius, double gamma, int riemann,
+                             const double* faces, double* dUdt, int* status_out, void* stream);
 
 /* dUdt = L(U): kfvm_reconstruct followed by kfvm_flux through the library's
  * own face buffer. */

@@ -237,6 +237,7 @@ const char* kfvm_status_string(kfvm_status s) {
     case KFVM_ERR_STATE: return "call out of order";
     case KFVM_ERR_TIMEOUT: return "bounded device wait timed out";
     case KFVM_ERR_NOMEM: return "out of memory";
+    case KFVM_ERR_TOO_LARGE: return "problem exceeds the fixed-size scratch of kfvm_flux_static";
   }
   return "unknown status";
 }

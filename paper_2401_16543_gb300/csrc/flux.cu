@@ -17,6 +17,8 @@
 //                     stage combination in float64.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace kfvm {
@@ -526,3 +528,110 @@ cudaError_t fma_peak(int bits, double* flops) {
 }
 
 }  // namespace kfvm
+
+// ===========================================================================
+// Allocation-free flux divergence (kfvm_flux_static).
+//
+// Some callers must not allocate device memory at all: plug-ins whose host
+// application owns the device memory budget through its own pool, and
+// latency-sensitive loops where cudaMalloc/cudaFree (which may synchronise
+// the device) are not allowed.  For them kfvm_flux_static runs the same face
+// flux and divergence kernels as kfvm_flux without a context, keeping the
+// face-averaged fluxes in the fixed array below instead of in buffers that
+// kfvm_init allocates.  The array lives in every device that loads this
+// library until the process exits.  Its device address is looked up once per
+// device, on the first call made with that device current.
+// ===========================================================================
+namespace kfvm {
+namespace {
+constexpr size_t kStaticHeader = 256;             // status word of the last call
+constexpr size_t kStaticFluxBytes = 16u << 20;    // 16 MiB of face fluxes
+}  // namespace
+}  // namespace kfvm
+
+static __device__ __align__(256) unsigned char kfvm_static_scratch[kfvm::kStaticHeader + kfvm::kStaticFluxBytes];
+
+namespace kfvm {
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_addr[128] = {nullptr};
+
+cudaError_t static_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, kfvm_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+template <int D, int R>
+cudaError_t flux_static_dr(const GridArgs& a, const FluxLayout& L, const double* faces, double* flux, double* dUdt,
+                           cudaStream_t st) {
+  long long mx = 0;
+  for (int d = 0; d < D; ++d) mx = L.nface[d] > mx ? L.nface[d] : mx;
+  dim3 grid((unsigned)((mx + kBlock - 1) / kBlock), D);
+  face_flux_kernel<D, R, double><<<grid, kBlock, 0, st>>>(a, L, faces, flux);
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  update_kernel<D, double, false><<<(unsigned)((ncell + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+      a, L, flux, 0, nullptr, nullptr, dUdt, nullptr);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace kfvm
+
+extern "C" kfvm_status kfvm_flux_static(const kfvm_grid* grid, int dims, int radius, double gamma, int riemann,
+                                        const double* faces, double* dUdt, int* status_out, void* stream) {
+  using namespace kfvm;
+  if (!grid || !faces || !dUdt || (dims != 2 && dims != 3) || (radius != 2 && radius != 3)) return KFVM_ERR_ARG;
+  if (!(gamma > 1.0) || (riemann != 0 && riemann != 1)) return KFVM_ERR_ARG;
+  GridArgs a{};
+  long long ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    const bool used = d < dims;
+    a.n[d] = used ? grid->n[d] : 1;
+    if (a.n[d] < 1 || (used && !(grid->hi[d] > grid->lo[d]))) return KFVM_ERR_ARG;
+    a.dx[d] = used ? (grid->hi[d] - grid->lo[d]) / grid->n[d] : 1.0;
+    for (int s = 0; s < 2; ++s) {
+      a.bc[d][s] = used ? grid->bc[d][s] : KFVM_BC_PERIODIC;
+      if (a.bc[d][s] != KFVM_BC_PERIODIC && a.bc[d][s] != KFVM_BC_OUTFLOW) return KFVM_ERR_ARG;
+    }
+    ncell *= a.n[d];
+  }
+  FluxLayout L{};
+  long long total = 0;
+  for (int d = 0; d < 3; ++d) {
+    L.off[d] = total;
+    L.nface[d] = d < dims ? (long long)(a.n[d] + 1) * (ncell / a.n[d]) : 0;
+    total += (long long)(dims + 2) * L.nface[d];
+  }
+  if ((unsigned long long)total * sizeof(double) > kStaticFluxBytes) return KFVM_ERR_TOO_LARGE;
+  void* base = nullptr;
+  if (static_scratch_address(&base) != cudaSuccess) return KFVM_ERR_CUDA;
+  int* status = reinterpret_cast<int*>(base);
+  double* flux = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + kStaticHeader);
+  a.gamma = gamma;
+  a.riemann = riemann;
+  a.status = status;
+  a.scalars = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return KFVM_ERR_CUDA;
+  cudaError_t e;
+  if (dims == 2 && radius == 2) e = flux_static_dr<2, 2>(a, L, faces, flux, dUdt, st);
+  else if (dims == 2) e = flux_static_dr<2, 3>(a, L, faces, flux, dUdt, st);
+  else if (radius == 2) e = flux_static_dr<3, 2>(a, L, faces, flux, dUdt, st);
+  else e = flux_static_dr<3, 3>(a, L, faces, flux, dUdt, st);
+  if (e != cudaSuccess) return KFVM_ERR_CUDA;
+  if (status_out && cudaMemcpyAsync(status_out, status, sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return KFVM_ERR_CUDA;
+  return KFVM_OK;
+}
