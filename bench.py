@@ -222,7 +222,7 @@ def main():
 
     path = args.path
     if path == "auto":
-        path = "fp64"
+        path = "fp32"
     sampler = ClockSampler(torch.cuda.current_device() if world == 1 else local)
     sampler.start()
     # ---- headline path, resident inputs ----

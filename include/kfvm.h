@@ -20,12 +20,14 @@
  * interior cells only (ghost cells are never stored).  Variables are
  * (rho, rho*u, rho*v, [rho*w,] E): nv = dims + 2.
  *
- * Face (Riemann) state layout: [point][var][cell] with point index
+ * Face (Riemann) state layout: point index
  * s = (dir*2 + side)*R^(dims-1) + t, side 0 the low face (x_dir = -1/2),
  * t = t0 + R*t1 over the transverse axes in increasing order and the
  * Gauss-Legendre nodes (R per face dimension, Sec. 5.1) ascending.  In the
- * FP64 precision mode the values are float64 conservative variables; in the
- * FP32 mode they are float32 PRIMITIVE variables (rho, u, v, [w,] p).
+ * FP64 precision mode the values are float64 conservative variables laid out
+ * [point][var][cell].  In the FP32 mode they are float32 PRIMITIVE variables:
+ * [point][cell] float4 (rho, u, v, p) and, in 3D, a following plane
+ * [point][cell] of w (F*nv*ncell floats in all).
  *
  * Errors: every call returns a kfvm_status; nothing throws across the ABI.
  * Device-side failures (a non-admissible state, a NaN) raise a device flag

@@ -194,6 +194,18 @@ class KFVM:
         _check(self._L.kfvm_reconstruct(self._ctx, _ptr(U), _ptr(faces), _stream(stream)), "kfvm_reconstruct")
         return faces
 
+    def faces_primitive(self, faces):
+        """FP32-mode Riemann states as a [F, nv, cells] float32 tensor of (rho, u, v[, w], p)."""
+        import torch
+        F, n = self.nface, self.ncell
+        flat = faces.reshape(-1)
+        a4 = flat[:F * n * 4].reshape(F, n, 4)
+        comps = [a4[..., 0], a4[..., 1], a4[..., 2]]
+        if self.dims == 3:
+            comps.append(flat[F * n * 4:F * n * 5].reshape(F, n))
+        comps.append(a4[..., 3])
+        return torch.stack(comps, dim=1)
+
     def flux(self, faces, dUdt=None, stream=None):
         import torch
         if dUdt is None:

@@ -415,8 +415,7 @@ kfvm_status kfvm_flux(kfvm_ctx* ctx, const void* faces, double* dUdt, void* stre
   if (s) return s;
   if (!faces || !dUdt) return KFVM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  KFVM_LAUNCH(ctx, kProfFaceFlux, st, launch_face_flux(ctx, faces, st));
-  KFVM_LAUNCH(ctx, kProfUpdate, st, launch_update(ctx, 0, nullptr, nullptr, dUdt, st));
+  KFVM_LAUNCH(ctx, kProfUpdate, st, launch_flux_update(ctx, 0, faces, nullptr, nullptr, dUdt, st));
   return KFVM_OK;
 }
 
@@ -443,8 +442,7 @@ kfvm_status kfvm_step(kfvm_ctx* ctx, double* U, double cfl, double t_remaining, 
       KFVM_LAUNCH(ctx, kProfRecon32, st, launch_recon32(ctx, in[k], ctx->d_shadow, (float*)ctx->d_faces, st));
     else
       KFVM_LAUNCH(ctx, kProfRecon64, st, launch_recon64(ctx, in[k], (double*)ctx->d_faces, st));
-    KFVM_LAUNCH(ctx, kProfFaceFlux, st, launch_face_flux(ctx, ctx->d_faces, st));
-    KFVM_LAUNCH(ctx, kProfUpdate, st, launch_update(ctx, k + 1, U, in[k], outp[k], st));
+    KFVM_LAUNCH(ctx, kProfUpdate, st, launch_flux_update(ctx, k + 1, ctx->d_faces, U, in[k], outp[k], st));
   }
   if (dt_out) {
     KFVM_TRY(cudaMemcpyAsync(dt_out, &ctx->d_scalars->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -469,8 +467,8 @@ kfvm_status kfvm_sync_status(kfvm_ctx* ctx, void* stream) {
 int kfvm_profile_count(void) { return kProfCount; }
 
 kfvm_status kfvm_profile_get(kfvm_ctx* ctx, int index, const char** name, long long* launches, double* ms) {
-  static const char* names[kProfCount] = {"max_rate", "recon64", "recon32", "face_flux", "update", "gate_mask",
-                                          "shadow"};
+  static const char* names[kProfCount] = {"max_rate", "recon64", "recon32", "face_flux", "flux_update",
+                                          "gate_mask", "shadow"};
   if (!ctx || index < 0 || index >= kProfCount) return KFVM_ERR_ARG;
   const bool done = prof_fold(ctx);
   if (name) *name = names[index];

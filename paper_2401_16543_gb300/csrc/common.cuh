@@ -20,6 +20,8 @@ struct GridArgs {
   int riemann;
   int* status;
   DevScalars* scalars;
+  // float32 copies for the mixed-precision kernels
+  float gammaf, epsf, lo_f, hi_f;
 };
 
 inline GridArgs make_grid_args(const kfvm_ctx* c) {
@@ -38,6 +40,10 @@ inline GridArgs make_grid_args(const kfvm_ctx* c) {
   g.riemann = c->riemann;
   g.status = c->d_status;
   g.scalars = c->d_scalars;
+  g.gammaf = (float)c->gamma;
+  g.epsf = (float)c->eps;
+  g.lo_f = (float)(1.0 - c->kappa + c->kappa * c->eta);
+  g.hi_f = (float)(1.0 + c->kappa - c->kappa * c->eta);
   return g;
 }
 
@@ -75,6 +81,13 @@ template <int D>
 __host__ __device__ constexpr double linear_weight(int q) {
   constexpr double ghi = 0.8, glo = 0.8;
   return q == 0 ? ghi : (q == 1 ? (1.0 - ghi) * glo : (1.0 - ghi) * (1.0 - glo) / (2 * D));
+}
+
+// 1/x in float64 from a float32 reciprocal refined by one Newton-Raphson step
+// (relative error below 1e-14 for normal x; Newton's iteration for 1/x).
+__device__ __forceinline__ double recip64(double x) {
+  const double r0 = (double)__frcp_rn((float)x);
+  return r0 * fma(-x, r0, 2.0);
 }
 
 __device__ __forceinline__ void raise_flag(int* status, int bit) {

@@ -15,6 +15,10 @@
 //                     average over the face.
 //   update_kernel     L = -sum_d (F_{d,+} - F_{d,-})/Delta_d and the Shu-Osher
 //                     stage combination in float64.
+//   flux_update_kernel  the hot path's fusion of the two: a CTA computes every
+//                     face flux of its tile once into shared memory, then the
+//                     divergence and the stage update of its cells.
+// The face-flux buffer kernels serve kfvm_flux_static.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -42,15 +46,32 @@ __global__ void __launch_bounds__(kBlock) max_rate_kernel(GridArgs a, const doub
       u[v] = U[v * ncell + c];
       if (SHADOW) shadow[v * ncell + c] = (float)u[v];
     }
-    const double ir = 1.0 / u[0];
-    double m2 = 0.0;
+    double rate;
+    if constexpr (SHADOW) {
+      // mixed-precision path: the pressure (E - |m|^2/(2 rho) cancels near vacuum) in
+      // float64, the sound speed and the rate in float32
+      const double ir = recip64(u[0]);
+      double m2 = 0.0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) m2 = fma(u[1 + k], u[1 + k], m2);
-    const double p = gm1 * (u[D + 1] - 0.5 * m2 * ir);
-    const double cs = sqrt(a.gamma * p * ir);
-    double rate = 0.0;
+      for (int k = 0; k < D; ++k) m2 = fma(u[1 + k], u[1 + k], m2);
+      const double p = gm1 * fma(-0.5 * m2, ir, u[D + 1]);
+      const float cs = sqrtf((float)(a.gamma * p * ir));
+      const float irf = (float)ir;
+      float r = 0.0f;
 #pragma unroll
-    for (int k = 0; k < D; ++k) rate += (fabs(u[1 + k] * ir) + cs) / a.dx[k];
+      for (int k = 0; k < D; ++k) r += (fabsf((float)u[1 + k] * irf) + cs) * (float)(1.0 / a.dx[k]);
+      rate = (p > 0.0 && u[0] > 0.0) ? (double)r : __longlong_as_double(0x7ff8000000000000LL);
+    } else {
+      const double ir = 1.0 / u[0];
+      double m2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) m2 = fma(u[1 + k], u[1 + k], m2);
+      const double p = gm1 * (u[D + 1] - 0.5 * m2 * ir);
+      const double cs = sqrt(a.gamma * p * ir);
+      rate = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) rate += (fabs(u[1 + k] * ir) + cs) / a.dx[k];
+    }
     if (!(rate <= best)) best = rate;  // NaN propagates
   }
   unsigned long long bits = __double_as_longlong(best);
@@ -271,27 +292,36 @@ struct FluxLayout {
   long long nface[3];
 };
 
+// Riemann state of point s of cell `cell`.  Float64 faces: conservative
+// [s][v][cell].  Float32 faces: primitive, [s][cell] float4 (rho, u, v, p)
+// followed in 3D by the plane [s][cell] of w.
+template <int D, int R>
+__device__ __forceinline__ void load_face(const double* __restrict__ f, int s, long long cell, long long ncell,
+                                          double* u) {
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) u[v] = f[((long long)s * (D + 2) + v) * ncell + cell];
+}
+template <int D, int R>
+__device__ __forceinline__ void load_face(const float* __restrict__ f, int s, long long cell, long long ncell,
+                                          float* u) {
+  constexpr int F = 2 * D * ipow(R, D - 1);
+  const float4 q = __ldg(reinterpret_cast<const float4*>(f) + (long long)s * ncell + cell);
+  u[0] = q.x;
+  u[1] = q.y;
+  u[2] = q.z;
+  if (D == 3) u[3] = __ldg(f + 4LL * F * ncell + (long long)s * ncell + cell);
+  u[D + 1] = q.w;
+}
+
+// Face-averaged numerical flux on the face between cell c - e_dir and cell c
+// (c[dir] in [0, n_dir]): exterior states at outflow boundaries copy the
+// interior one, periodic faces see the wrapped neighbour; R^(d-1) Gauss points.
 template <int D, int R, typename Real>
-__global__ void __launch_bounds__(kBlock) face_flux_kernel(GridArgs a, FluxLayout L, const Real* __restrict__ faces,
-                                                           Real* __restrict__ flux) {
+__device__ __forceinline__ bool face_flux_at(const GridArgs& a, const Real* __restrict__ faces, int dir, const int* c,
+                                             long long ncell, Real* acc) {
   constexpr int NV = D + 2, NT = ipow(R, D - 1);
-  const int dir = blockIdx.y;
-  const long long nf = L.nface[dir];
-  const long long f = blockIdx.x * (long long)kBlock + threadIdx.x;
-  if (f >= nf) return;
-  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
-  // face coordinates in the grid extended by one along dir
-  int e[3] = {a.n[0], a.n[1], a.n[2]};
-  e[dir] += 1;
-  long long r = f;
-  int c[3];
-  c[0] = (int)(r % e[0]);
-  r /= e[0];
-  c[1] = (int)(r % e[1]);
-  c[2] = (int)(r / e[1]);
   const int nd = a.n[dir];
   const int i = c[dir];
-  // cells on both sides (-1 = outside an outflow boundary)
   int cl[3] = {c[0], c[1], c[2]}, cr[3] = {c[0], c[1], c[2]};
   cl[dir] = i - 1;
   cr[dir] = i;
@@ -306,7 +336,6 @@ __global__ void __launch_bounds__(kBlock) face_flux_kernel(GridArgs a, FluxLayou
   const long long rcell = ((long long)cr[2] * a.n[1] + cr[1]) * a.n[0] + cr[0];
   constexpr double w2[2] = {0.5, 0.5};
   constexpr double w3[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
-  Real acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = Real(0);
   bool ok = true;
@@ -314,12 +343,12 @@ __global__ void __launch_bounds__(kBlock) face_flux_kernel(GridArgs a, FluxLayou
   for (int t = 0; t < NT; ++t) {
     const int s_hi = (dir * 2 + 1) * NT + t, s_lo = (dir * 2) * NT + t;
     Real uL[NV], uR[NV], fl[NV];
+    if (has_l) load_face<D, R>(faces, s_hi, lcell, ncell, uL);
+    if (has_r) load_face<D, R>(faces, s_lo, rcell, ncell, uR);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const Real l = has_l ? faces[((long long)s_hi * NV + v) * ncell + lcell] : Real(0);
-      const Real rr = has_r ? faces[((long long)s_lo * NV + v) * ncell + rcell] : Real(0);
-      uL[v] = has_l ? l : rr;
-      uR[v] = has_r ? rr : l;
+      if (!has_l) uL[v] = uR[v];
+      if (!has_r) uR[v] = uL[v];
     }
     if constexpr (sizeof(Real) == 8)
       ok &= riemann64<D>(uL, uR, dir, a.gamma, a.riemann, fl);
@@ -329,9 +358,139 @@ __global__ void __launch_bounds__(kBlock) face_flux_kernel(GridArgs a, FluxLayou
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] += Real(wt) * fl[v];
   }
-  if (!ok) raise_flag(a.status, kFlagNonphysical);
+  return ok;
+}
+
+template <int D, int R, typename Real>
+__global__ void __launch_bounds__(kBlock) face_flux_kernel(GridArgs a, FluxLayout L, const Real* __restrict__ faces,
+                                                           Real* __restrict__ flux) {
+  constexpr int NV = D + 2;
+  const int dir = blockIdx.y;
+  const long long nf = L.nface[dir];
+  const long long f = blockIdx.x * (long long)kBlock + threadIdx.x;
+  if (f >= nf) return;
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  // face coordinates in the grid extended by one along dir
+  int e[3] = {a.n[0], a.n[1], a.n[2]};
+  e[dir] += 1;
+  long long r = f;
+  int c[3];
+  c[0] = (int)(r % e[0]);
+  r /= e[0];
+  c[1] = (int)(r % e[1]);
+  c[2] = (int)(r / e[1]);
+  Real acc[NV];
+  if (!face_flux_at<D, R, Real>(a, faces, dir, c, ncell, acc)) raise_flag(a.status, kFlagNonphysical);
 #pragma unroll
   for (int v = 0; v < NV; ++v) flux[L.off[dir] + v * nf + f] = acc[v];
+}
+
+// ---------------------------------------------------------------------------
+// Fused flux divergence and SSP-RK3 stage (the hot-path version): a CTA owns a
+// tile of cells, computes every face flux touching the tile exactly once into
+// shared memory (the tile's high faces by its last cells), then each thread
+// forms L = -sum_d (F_hi - F_lo)/Delta_d for its cell and the stage update.
+// Float64 faces: L and the update in float64 (the plain path).  Float32 faces:
+// L in float32, the stage combination accumulated in float64.
+// ---------------------------------------------------------------------------
+template <int D>
+struct FTile {
+  static constexpr int TX = (D == 2) ? 32 : 8, TY = 8, TZ = (D == 2) ? 1 : 4;
+  static constexpr int THREADS = TX * TY * TZ;
+  static constexpr int NF0 = (TX + 1) * TY * TZ, NF1 = TX * (TY + 1) * TZ, NF2 = (D == 3) ? TX * TY * (TZ + 1) : 0;
+  static constexpr int NF = NF0 + NF1 + NF2;
+  __host__ __device__ static constexpr int off(int d) { return d == 0 ? 0 : (d == 1 ? NF0 : NF0 + NF1); }
+  // index of face with local coordinates (x, y, z) in direction d's array
+  __device__ static int idx(int d, int x, int y, int z) {
+    const int ex = TX + (d == 0), ey = TY + (d == 1);
+    return off(d) + x + ex * (y + ey * z);
+  }
+};
+
+template <int D, int R, typename Real, bool SHADOW>
+__global__ void __launch_bounds__(FTile<D>::THREADS) flux_update_kernel(GridArgs a, const Real* __restrict__ faces,
+                                                                        int stage, const double* __restrict__ U0,
+                                                                        const double* __restrict__ Us,
+                                                                        double* __restrict__ out,
+                                                                        float* __restrict__ shadow) {
+  using T = FTile<D>;
+  constexpr int NV = D + 2;
+  __shared__ Real sflux[NV][T::NF];
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  const int tiles_x = (a.n[0] + T::TX - 1) / T::TX, tiles_y = (a.n[1] + T::TY - 1) / T::TY;
+  int b = blockIdx.x;
+  const int bx = b % tiles_x;
+  b /= tiles_x;
+  const int by = b % tiles_y;
+  const int bz = b / tiles_y;
+  const int tid = threadIdx.x;
+  const int l[3] = {tid % T::TX, (tid / T::TX) % T::TY, tid / (T::TX * T::TY)};
+  const int c[3] = {bx * T::TX + l[0], by * T::TY + l[1], (D == 3) ? bz * T::TZ + l[2] : 0};
+  const bool active = c[0] < a.n[0] && c[1] < a.n[1] && c[2] < a.n[2];
+  const int tdim[3] = {T::TX, T::TY, T::TZ};
+  if (active) {
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      Real f[NV];
+      ok &= face_flux_at<D, R, Real>(a, faces, d, c, ncell, f);
+      const int i0 = T::idx(d, l[0], l[1], l[2]);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sflux[v][i0] = f[v];
+      if (l[d] == tdim[d] - 1 || c[d] == a.n[d] - 1) {
+        int ch[3] = {c[0], c[1], c[2]}, lh[3] = {l[0], l[1], l[2]};
+        ch[d] += 1;
+        lh[d] += 1;
+        ok &= face_flux_at<D, R, Real>(a, faces, d, ch, ncell, f);
+        const int i1 = T::idx(d, lh[0], lh[1], lh[2]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sflux[v][i1] = f[v];
+      }
+    }
+    if (!ok) raise_flag(a.status, kFlagNonphysical);
+  }
+  __syncthreads();
+  if (!active) return;
+  const long long cidx = ((long long)c[2] * a.n[1] + c[1]) * a.n[0] + c[0];
+  Real Lv[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Lv[v] = Real(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    int lh[3] = {l[0], l[1], l[2]};
+    lh[d] += 1;
+    const int ilo = T::idx(d, l[0], l[1], l[2]), ihi = T::idx(d, lh[0], lh[1], lh[2]);
+    const Real idx = Real(1.0 / a.dx[d]);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Lv[v] = fma(sflux[v][ilo], idx, Lv[v]);
+      Lv[v] = fma(-sflux[v][ihi], idx, Lv[v]);
+    }
+  }
+  if (stage == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * ncell + cidx] = (double)Lv[v];
+    return;
+  }
+  const double dt = a.scalars->dt;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const long long i = v * ncell + cidx;
+    double res;
+    if constexpr (sizeof(Real) == 8) {
+      if (stage == 1) res = fma(dt, Lv[v], U0[i]);
+      else if (stage == 2) res = 0.75 * U0[i] + 0.25 * fma(dt, Lv[v], Us[i]);
+      else res = (1.0 / 3.0) * U0[i] + (2.0 / 3.0) * fma(dt, Lv[v], Us[i]);
+    } else {
+      // increment dt*L formed in float32, accumulated in float64
+      const double inc = (double)((float)dt * Lv[v]);
+      if (stage == 1) res = U0[i] + inc;
+      else if (stage == 2) res = fma(0.75, U0[i], 0.25 * (Us[i] + inc));
+      else res = fma(1.0 / 3.0, U0[i], (2.0 / 3.0) * (Us[i] + inc));
+    }
+    out[i] = res;
+    if (SHADOW) shadow[i] = (float)res;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -414,6 +573,27 @@ cudaError_t face_flux_dr(kfvm_ctx* ctx, const void* faces, cudaStream_t st) {
     face_flux_kernel<D, R, double><<<grid, kBlock, 0, st>>>(a, L, (const double*)faces, ctx->d_flux);
   else
     face_flux_kernel<D, R, float><<<grid, kBlock, 0, st>>>(a, L, (const float*)faces, (float*)ctx->d_flux);
+  ctx->launches += 1;
+  return cudaGetLastError();
+}
+
+template <int D, int R>
+cudaError_t flux_update_dr(kfvm_ctx* ctx, int stage, const void* faces, const double* U0, const double* Us,
+                           double* out, cudaStream_t st) {
+  using T = FTile<D>;
+  const GridArgs a = make_grid_args(ctx);
+  const unsigned tiles = (unsigned)(((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
+                                    ((D == 3) ? (ctx->n[2] + T::TZ - 1) / T::TZ : 1));
+  const bool shadow = ctx->precision == 32 && stage >= 1 && stage <= 2;
+  if (ctx->precision == 64)
+    flux_update_kernel<D, R, double, false><<<tiles, T::THREADS, 0, st>>>(a, (const double*)faces, stage, U0, Us, out,
+                                                                         nullptr);
+  else if (shadow)
+    flux_update_kernel<D, R, float, true><<<tiles, T::THREADS, 0, st>>>(a, (const float*)faces, stage, U0, Us, out,
+                                                                       ctx->d_shadow);
+  else
+    flux_update_kernel<D, R, float, false><<<tiles, T::THREADS, 0, st>>>(a, (const float*)faces, stage, U0, Us, out,
+                                                                        nullptr);
   ctx->launches += 1;
   return cudaGetLastError();
 }
@@ -521,6 +701,14 @@ cudaError_t launch_update(kfvm_ctx* ctx, int stage, const double* U0, const doub
                           cudaStream_t st) {
   if (ctx->dims == 2) return update_d<2>(ctx, stage, U0, Us, out, st);
   return update_d<3>(ctx, stage, U0, Us, out, st);
+}
+
+cudaError_t launch_flux_update(kfvm_ctx* ctx, int stage, const void* faces, const double* U0, const double* Us,
+                               double* out, cudaStream_t st) {
+  if (ctx->dims == 2 && ctx->R == 2) return flux_update_dr<2, 2>(ctx, stage, faces, U0, Us, out, st);
+  if (ctx->dims == 2 && ctx->R == 3) return flux_update_dr<2, 3>(ctx, stage, faces, U0, Us, out, st);
+  if (ctx->dims == 3 && ctx->R == 2) return flux_update_dr<3, 2>(ctx, stage, faces, U0, Us, out, st);
+  return flux_update_dr<3, 3>(ctx, stage, faces, U0, Us, out, st);
 }
 
 cudaError_t fma_peak(int bits, double* flops) {

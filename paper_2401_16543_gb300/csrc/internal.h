@@ -98,6 +98,9 @@ cudaError_t launch_face_flux(kfvm_ctx* ctx, const void* faces, cudaStream_t st);
 // stage: 0 -> dUdt only (to out), 1/2/3 -> SSP-RK3 stages writing the new state to out.
 cudaError_t launch_update(kfvm_ctx* ctx, int stage, const double* U0, const double* Us, double* out, cudaStream_t st);
 cudaError_t launch_shadow(kfvm_ctx* ctx, const double* U, float* shadow, cudaStream_t st);
+// Fused face fluxes + divergence + stage update (stage 0: write dUdt to out).
+cudaError_t launch_flux_update(kfvm_ctx* ctx, int stage, const void* faces, const double* U0, const double* Us,
+                               double* out, cudaStream_t st);
 cudaError_t launch_gate_mask(kfvm_ctx* ctx, const double* U, cudaStream_t st);
 cudaError_t launch_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, cudaStream_t st);
 cudaError_t launch_gate_forward(kfvm_ctx* ctx, const float* X, float* prob, size_t n, cudaStream_t st);

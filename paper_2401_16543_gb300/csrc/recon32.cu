@@ -1,12 +1,17 @@
-// recon32.cu -- FP32 Riemann states of the mixed-precision path (placeholder until built).
-#include <cuda_runtime.h>
-
-#include "common.cuh"
+// recon32.cu -- dispatch of the FP32 Riemann-state kernels over (d, R).
+#include "internal.h"
 
 namespace kfvm {
 
-cudaError_t launch_recon32(kfvm_ctx*, const double*, const float*, float*, cudaStream_t) {
-  return cudaErrorNotSupported;
+cudaError_t launch_recon32_22(kfvm_ctx*, const double*, const float*, float*, cudaStream_t);
+cudaError_t launch_recon32_23(kfvm_ctx*, const double*, const float*, float*, cudaStream_t);
+cudaError_t launch_recon32_32(kfvm_ctx*, const double*, const float*, float*, cudaStream_t);
+
+cudaError_t launch_recon32(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st) {
+  if (ctx->dims == 2 && ctx->R == 2) return launch_recon32_22(ctx, U, shadow, faces, st);
+  if (ctx->dims == 2 && ctx->R == 3) return launch_recon32_23(ctx, U, shadow, faces, st);
+  if (ctx->dims == 3 && ctx->R == 2) return launch_recon32_32(ctx, U, shadow, faces, st);
+  return cudaErrorNotSupported;  // d = 3, R = 3: the float32 tables exceed the kernel-parameter space
 }
 
 }  // namespace kfvm

@@ -1,0 +1,389 @@
+// recon32.cuh -- FP32 Riemann states of the mixed-precision path (Sec. 5.3 steps 1-3).
+//
+// Same mathematics as recon64 (Sec. 3, Sec. 4), arranged for the FP32 pipe:
+//   * the CTA stages a float32 shadow of its tile of cell averages (+ halo R);
+//   * the stencil is transformed to linearized primitive variables RELATIVE
+//     to the central cell, dW_h = Phi (U_h - U_c) (Eq. 33); since every
+//     reconstruction vector sums to one and the WENO-AO coefficients sum to
+//     one, w_s = W_c + (reconstruction of dW), with W_c = (rho~, 0, p~);
+//   * contractions with compile-time indices (C++17 fold expressions over the
+//     stencil tables) so the stencil stays in registers and the weights are
+//     constant-bank operands;
+//   * nonlinear weights in the scaled form omega_q ~ gamma_q/((beta_q/beta_max)^2
+//     + eps/beta_max^2), identical in exact arithmetic to Eq. 24 (eps = 1e-40 is
+//     subnormal in float32);
+//   * the pressure at a face point follows without cancellation from the
+//     linearized primitive values: p_s = pi_s - (gamma-1) rho~^2 |du_s|^2 / (2 rho_s),
+//     and the positivity limiter (Sec. 4) works on the same quantities
+//     (the blend toward the cell average is linear, so it is a scaling of dW);
+//   * only the central pressure p~ is recovered in float64 (E - |m|^2/(2 rho)
+//     cancels near vacuum), with a float32 reciprocal refined by one Newton step.
+// Output: float32 primitive (rho, u, [v, w,] p) Riemann states.
+// In the gated mode the cells the gate marks smooth take the linear S0
+// reconstruction; the others are compacted within the CTA so that whole warps
+// run WENO-AO.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <utility>
+
+#include "common.cuh"
+
+namespace kfvm {
+namespace r32 {
+
+template <int D, int R>
+struct T32 {
+  static constexpr int TX = (D == 2) ? 32 : 8;
+  static constexpr int TY = (D == 2) ? 8 : 8;
+  static constexpr int TZ = (D == 2) ? 1 : 2;
+  static constexpr int H = R;
+  static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SZ = (D == 2) ? 1 : TZ + 2 * H;
+  static constexpr int SN = SX * SY * SZ;
+  static constexpr int THREADS = TX * TY * TZ;
+};
+
+// compile-time views of the stencil tables (scalar constexpr members are usable in device code)
+template <int D, int R, int Q, int J>
+struct SIdx {
+  static constexpr int v = Geo<D, R>::tab.idx[Q][J];
+};
+template <int D, int R, int Q>
+struct SLen {
+  static constexpr int v = Geo<D, R>::tab.len[Q];
+};
+template <int D, int R, int Q>
+struct WOff {
+  static constexpr int v = Geo<D, R>::woff(Q);
+};
+template <int D, int R, int L>
+struct Dlt {
+  static constexpr int v = Geo<D, R>::tab.off[L][0] +
+                           T32<D, R>::SX * (Geo<D, R>::tab.off[L][1] + T32<D, R>::SY * Geo<D, R>::tab.off[L][2]);
+};
+
+template <int D, int R>
+struct W32 {
+  float w[Geo<D, R>::WCOUNT];
+};
+
+// r . g over substencil Q with the weight row starting at OFF
+template <int D, int R, int Q, int OFF, int... J>
+__device__ __forceinline__ float dot_q(const W32<D, R>& W, const float (&g)[Geo<D, R>::N0],
+                                       std::integer_sequence<int, J...>) {
+  float acc = 0.0f;
+  ((acc = fmaf(W.w[OFF + J], g[SIdx<D, R, Q, J>::v], acc)), ...);
+  return acc;
+}
+
+template <int D, int R, int Q, int M_>
+__device__ __forceinline__ float deriv(const W32<D, R>& W, const float (&g)[Geo<D, R>::N0]) {
+  constexpr int n = SLen<D, R, Q>::v;
+  return dot_q<D, R, Q, WOff<D, R, Q>::v + Geo<D, R>::F * n + M_ * n>(W, g, std::make_integer_sequence<int, n>{});
+}
+
+template <int D, int R, int Q, int... Ms>
+__device__ __forceinline__ float beta_q(const W32<D, R>& W, const float (&g)[Geo<D, R>::N0],
+                                        std::integer_sequence<int, Ms...>) {
+  float b = 0.0f, t = 0.0f;
+  ((t = deriv<D, R, Q, Ms>(W, g), b = fmaf(t, t, b)), ...);
+  return b;
+}
+
+template <int D, int R, int Q, int S>
+__device__ __forceinline__ float face_q(const W32<D, R>& W, const float (&g)[Geo<D, R>::N0]) {
+  constexpr int n = SLen<D, R, Q>::v;
+  return dot_q<D, R, Q, WOff<D, R, Q>::v + S * n>(W, g, std::make_integer_sequence<int, n>{});
+}
+
+template <int D, int R, int S, int... Qs>
+__device__ __forceinline__ float face_blend(const W32<D, R>& W, const float (&g)[Geo<D, R>::N0],
+                                            const float (&coef)[Geo<D, R>::NQ], std::integer_sequence<int, Qs...>) {
+  float acc = 0.0f;
+  ((acc = fmaf(coef[Qs], face_q<D, R, Qs, S>(W, g), acc)), ...);
+  return acc;
+}
+
+template <int D, int R, int... Qs>
+__device__ __forceinline__ void all_betas(const W32<D, R>& W, const float (&g)[Geo<D, R>::N0],
+                                          float (&beta)[Geo<D, R>::NQ], std::integer_sequence<int, Qs...>) {
+  ((beta[Qs] = beta_q<D, R, Qs>(W, g, std::make_integer_sequence<int, Geo<D, R>::M>{})), ...);
+}
+
+template <int D, int R, int... Ss>
+__device__ __forceinline__ void all_faces_weno(const W32<D, R>& W, const float (&g)[Geo<D, R>::N0],
+                                               const float (&coef)[Geo<D, R>::NQ], float* out, int stride,
+                                               std::integer_sequence<int, Ss...>) {
+  ((out[Ss * stride] = face_blend<D, R, Ss>(W, g, coef, std::make_integer_sequence<int, Geo<D, R>::NQ>{})), ...);
+}
+
+template <int D, int R, int... Ss>
+__device__ __forceinline__ void all_faces_linear(const W32<D, R>& W, const float (&g)[Geo<D, R>::N0], float* out,
+                                                 int stride, std::integer_sequence<int, Ss...>) {
+  ((out[Ss * stride] = face_q<D, R, 0, Ss>(W, g)), ...);
+}
+
+// load dW (row v of Phi applied to U_l - U_c) for every S0 cell into g
+template <int D, int R, int... Ls>
+__device__ __forceinline__ void gather_row(const float* __restrict__ sm, int c, int v, float (&g)[Geo<D, R>::N0],
+                                           const float* uc, const float* ut, float kin, float irt, float gm1,
+                                           std::integer_sequence<int, Ls...>) {
+  constexpr int SN = T32<D, R>::SN;
+  if (v == 0) {
+    ((g[Ls] = sm[c + Dlt<D, R, Ls>::v] - uc[0]), ...);
+  } else if (v <= D) {
+    const float uv = (v == 1) ? ut[0] : (v == 2 ? ut[1] : ut[D == 3 ? 2 : 1]);
+    ((g[Ls] = (fmaf(-uv, sm[c + Dlt<D, R, Ls>::v] - uc[0], sm[v * SN + c + Dlt<D, R, Ls>::v] - uc[v])) * irt), ...);
+  } else {
+    auto pr = [&](int o) {
+      float t = fmaf(kin, sm[o] - uc[0], sm[(D + 1) * SN + o] - uc[D + 1]);
+#pragma unroll
+      for (int k = 0; k < D; ++k) t = fmaf(-ut[k], sm[(1 + k) * SN + o] - uc[1 + k], t);
+      return gm1 * t;
+    };
+    ((g[Ls] = pr(c + Dlt<D, R, Ls>::v)), ...);
+  }
+}
+
+template <int D, int R>
+__global__ void __launch_bounds__(T32<D, R>::THREADS) recon32_kernel(GridArgs a, int mode,
+                                                                     const double* __restrict__ U,
+                                                                     const float* __restrict__ S,
+                                                                     float* __restrict__ faces,
+                                                                     const unsigned char* __restrict__ gate_mask,
+                                                                     const __grid_constant__ W32<D, R> W) {
+  using G = Geo<D, R>;
+  using T = T32<D, R>;
+  constexpr int NV = G::NV, SN = T::SN, F = G::F, NQ = G::NQ, N0 = G::N0, TH = T::THREADS;
+  extern __shared__ float smem32[];
+  float* sm = smem32;                 // [NV][SN] shadow cell averages
+  float* sp = sm + NV * SN;           // [SN] float32 pressures (limiter bounds)
+  float* dw = sp + SN;                // [F*NV][TH] reconstructed dW per cell of the tile
+  int* list = reinterpret_cast<int*>(dw + F * NV * TH);  // [TH] compacted WENO cells
+  __shared__ int s_count;
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  const float gm1 = a.gammaf - 1.0f;
+
+  const int tiles_x = (a.n[0] + T::TX - 1) / T::TX, tiles_y = (a.n[1] + T::TY - 1) / T::TY;
+  int b = blockIdx.x;
+  const int bx = b % tiles_x;
+  b /= tiles_x;
+  const int by = b % tiles_y;
+  const int bz = b / tiles_y;
+  const int x0 = bx * T::TX - T::H, y0 = by * T::TY - T::H, z0 = (D == 3) ? bz * T::TZ - T::H : 0;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_count = 0;
+
+  for (int i = tid; i < SN; i += TH) {
+    const int sx = i % T::SX, sy = (i / T::SX) % T::SY, sz = i / (T::SX * T::SY);
+    const int gx = map_index(x0 + sx, a.n[0], a.bc[0][0], a.bc[0][1]);
+    const int gy = map_index(y0 + sy, a.n[1], a.bc[1][0], a.bc[1][1]);
+    const int gz = (D == 3) ? map_index(z0 + sz, a.n[2], a.bc[2][0], a.bc[2][1]) : 0;
+    const long long gc = ((long long)gz * a.n[1] + gy) * a.n[0] + gx;
+    float u[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      u[v] = S[v * ncell + gc];
+      sm[v * SN + i] = u[v];
+    }
+    float m2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) m2 = fmaf(u[1 + k], u[1 + k], m2);
+    sp[i] = gm1 * fmaf(-0.5f * m2, __frcp_rn(u[0]), u[D + 1]);
+  }
+  __syncthreads();
+
+  const int lx = tid % T::TX, ly = (tid / T::TX) % T::TY, lz = tid / (T::TX * T::TY);
+  const int x = bx * T::TX + lx, y = by * T::TY + ly, z = (D == 3) ? bz * T::TZ + lz : 0;
+  const bool active = x < a.n[0] && y < a.n[1] && z < a.n[2];
+  const long long cell = active ? ((long long)z * a.n[1] + y) * a.n[0] + x : 0;
+  const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (D == 3 ? lz + T::H : 0));
+  float* mydw = dw + tid;
+  constexpr auto SEQ_L = std::make_integer_sequence<int, N0>{};
+  constexpr auto SEQ_S = std::make_integer_sequence<int, F>{};
+
+  // reference state of the cell
+  auto cell_ref = [&](int cc, float* uc, float* ut, float& kin, float& irt) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) uc[v] = sm[v * SN + cc];
+    irt = __frcp_rn(uc[0]);
+    kin = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      ut[k] = uc[1 + k] * irt;
+      kin = fmaf(ut[k], ut[k], kin);
+    }
+    kin *= 0.5f;
+  };
+
+  // ---- phase 1: linear cells (all cells in the linear mode) ----
+  bool weno_here = active && (mode == 0 || (mode == 2 && !gate_mask[cell]));
+  if (active && !weno_here) {
+    float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
+    cell_ref(c, uc, ut, kin, irt);
+    float g[N0];
+#pragma unroll 1
+    for (int v = 0; v < NV; ++v) {
+      gather_row<D, R>(sm, c, v, g, uc, ut, kin, irt, gm1, SEQ_L);
+      all_faces_linear<D, R>(W, g, mydw + v * TH, NV * TH, SEQ_S);
+    }
+  }
+  // ---- phase 2: WENO-AO cells, compacted within the CTA ----
+  if (mode == 0) {
+    // every active cell is a WENO cell: no compaction needed
+  } else {
+    if (weno_here) list[atomicAdd(&s_count, 1)] = tid;
+  }
+  __syncthreads();
+  const int nweno = (mode == 0) ? TH : s_count;
+  for (int k = tid; k < nweno; k += TH) {
+    const int owner = (mode == 0) ? k : list[k];
+    if (mode == 0 && !active) continue;
+    const int olx = owner % T::TX, oly = (owner / T::TX) % T::TY, olz = owner / (T::TX * T::TY);
+    const int oc = (olx + T::H) + T::SX * ((oly + T::H) + T::SY * (D == 3 ? olz + T::H : 0));
+    float* odw = dw + owner;
+    float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
+    cell_ref(oc, uc, ut, kin, irt);
+    float g[N0];
+#pragma unroll 1
+    for (int v = 0; v < NV; ++v) {
+      gather_row<D, R>(sm, oc, v, g, uc, ut, kin, irt, gm1, SEQ_L);
+      float beta[NQ];
+      all_betas<D, R>(W, g, beta, std::make_integer_sequence<int, NQ>{});
+      float bmax = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) bmax = fmaxf(bmax, beta[q]);
+      float coef[NQ];
+      if (bmax > 0.0f) {
+        const float ib = __frcp_rn(bmax);
+        const float e = fmaxf(a.epsf * ib * ib, 1e-30f);
+        float om[NQ], sum = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const float bq = beta[q] * ib;
+          om[q] = __fdividef((float)linear_weight<D>(q), fmaf(bq, bq, e));
+          sum += om[q];
+        }
+        const float inv = __frcp_rn(sum);
+        const float w0 = om[0] * inv;
+        coef[0] = w0 / (float)linear_weight<D>(0);
+#pragma unroll
+        for (int q = 1; q < NQ; ++q)
+          coef[q] = fmaf(-w0, (float)(linear_weight<D>(q) / linear_weight<D>(0)), om[q] * inv);
+      } else {
+        coef[0] = 1.0f;
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
+      }
+      all_faces_weno<D, R>(W, g, coef, odw + v * TH, NV * TH, SEQ_S);
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+
+  // ---- tail: central pressure in float64, limiter, primitive Riemann states ----
+  float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
+  cell_ref(c, uc, ut, kin, irt);
+  float pt;
+  {
+    double m2 = 0.0, u8[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u8[v] = U[v * ncell + cell];
+#pragma unroll
+    for (int k = 0; k < D; ++k) m2 = fma(u8[1 + k], u8[1 + k], m2);
+    const double p8 = (a.gamma - 1.0) * fma(-0.5 * m2, recip64(u8[0]), u8[D + 1]);
+    pt = (float)p8;
+    if (!(u8[0] > 0.0) || !(p8 > 0.0)) raise_flag(a.status, kFlagNonphysical);
+  }
+  const float rt = uc[0];
+  const float cq = 0.5f * gm1 * rt * rt;  // (gamma-1) rho~^2 / 2
+  float th = 1.0f, thp = 1.0f;
+  if (a.positivity) {
+    float rmax = -3.0e38f, rmin = 3.0e38f, pmin = 3.0e38f;
+#pragma unroll
+    for (int k = (D == 3 ? -1 : 0); k <= (D == 3 ? 1 : 0); ++k)
+#pragma unroll
+      for (int j = -1; j <= 1; ++j)
+#pragma unroll
+        for (int i = -1; i <= 1; ++i) {
+          const int o = c + i + T::SX * (j + T::SY * k);
+          rmax = fmaxf(rmax, sm[o]);
+          rmin = fminf(rmin, sm[o]);
+          pmin = fminf(pmin, sp[o]);
+        }
+    const float rho_max = rmax * a.hi_f, rho_min = rmin * a.lo_f, p_min = pmin * a.lo_f;
+#pragma unroll
+    for (int s = 0; s < F; ++s) {
+      const float drs = mydw[(s * NV) * TH];
+      const float rs = rt + drs;
+      if (rs < rho_min) th = fminf(th, (rt - rho_min) / (rt - rs));
+      if (rs > rho_max) th = fminf(th, (rho_max - rt) / (rs - rt));
+    }
+    // p(theta) >= p_min  <=>  (pt + theta dpi - p_min) (rt + theta drho) >= cq theta^2 |du|^2
+    auto admissible = [&](float t, float dr, float dp, float du2) {
+      const float rr = fmaf(t, dr, rt);
+      return rr > 0.0f && (fmaf(t, dp, pt) - p_min) * rr >= cq * t * t * du2;
+    };
+#pragma unroll 1
+    for (int s = 0; s < F; ++s) {
+      const float dr = th * mydw[(s * NV) * TH];
+      const float dp = th * mydw[(s * NV + NV - 1) * TH];
+      float du2 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float du = th * mydw[(s * NV + 1 + k) * TH];
+        du2 = fmaf(du, du, du2);
+      }
+      if (admissible(1.0f, dr, dp, du2)) continue;
+      float lo = 0.0f, hi = 1.0f;
+#pragma unroll 1
+      for (int it = 0; it < 40; ++it) {
+        const float mid = 0.5f * (lo + hi);
+        if (admissible(mid, dr, dp, du2)) lo = mid; else hi = mid;
+      }
+      thp = fminf(thp, lo);
+    }
+  }
+  const float sc = th * thp;
+  float4* out4 = reinterpret_cast<float4*>(faces);
+#pragma unroll 1
+  for (int s = 0; s < F; ++s) {
+    const float dr = sc * mydw[(s * NV) * TH];
+    const float rs = rt + dr;
+    const float irs = __frcp_rn(rs);
+    float du2 = 0.0f, uo[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float du = sc * mydw[(s * NV + 1 + k) * TH];
+      du2 = fmaf(du, du, du2);
+      uo[k] = fmaf(rt * du, irs, ut[k]);
+    }
+    const float dp = sc * mydw[(s * NV + NV - 1) * TH];
+    const float ps = fmaf(-cq * du2, irs, pt + dp);
+    // float32 layout: [s][cell] float4 (rho, u, v, p), then (3D) the plane [s][cell] of w
+    out4[(long long)s * ncell + cell] = make_float4(rs, uo[0], uo[1], ps);
+    if (D == 3) faces[4LL * F * ncell + (long long)s * ncell + cell] = uo[D == 3 ? 2 : 0];
+  }
+}
+
+template <int D, int R>
+cudaError_t launch(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st) {
+  using T = T32<D, R>;
+  using G = Geo<D, R>;
+  const GridArgs a = make_grid_args(ctx);
+  const int tiles = ((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
+                    ((D == 3) ? (ctx->n[2] + T::TZ - 1) / T::TZ : 1);
+  const size_t smem = sizeof(float) * ((G::NV + 1) * T::SN + G::F * G::NV * T::THREADS) + sizeof(int) * T::THREADS;
+  auto kern = recon32_kernel<D, R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  std::unique_ptr<W32<D, R>> wp(new W32<D, R>);
+  for (int i = 0; i < G::WCOUNT; ++i) wp->w[i] = (float)ctx->w_host[i];
+  kern<<<tiles, T::THREADS, smem, st>>>(a, ctx->recon, U, shadow, faces, ctx->d_gate_mask, *wp);
+  ctx->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace r32
+}  // namespace kfvm

@@ -1,0 +1,10 @@
+// recon32_23.cu -- FP32 Riemann states for d = 2, R = 3 (one instantiation per
+// translation unit so that the library compiles in parallel).
+#include "recon32.cuh"
+
+namespace kfvm {
+cudaError_t launch_recon32_23(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces,
+                                cudaStream_t st) {
+  return r32::launch<2, 3>(ctx, U, shadow, faces, st);
+}
+}  // namespace kfvm
