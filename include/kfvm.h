@@ -214,6 +214,19 @@ kfvm_status kfvm_gate_get_params(kfvm_ctx* ctx, float* host_params, size_t count
  * smooth), else 0. */
 kfvm_status kfvm_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, void* stream);
 
+/* The smooth mask the gated step computes from U with the loaded network
+ * (device, one byte per cell, 1 = the network's probability exceeds
+ * "gate_threshold"), written to mask_out (device).  In the FP32 mode the
+ * features come from the float32 copy of U, as in the step. */
+kfvm_status kfvm_gate_mask(kfvm_ctx* ctx, const double* U, unsigned char* mask_out, void* stream);
+
+/* Use a caller-supplied smooth mask (device, one byte per cell, 1 = linear
+ * reconstruction, 0 = WENO-AO) instead of the network: sets the gated mode
+ * ("recon" 3) with this mask until "recon" is set again.  Lets another
+ * troubled-cell indicator drive the gated path, and tests compare the gated
+ * path with the oracle on one mask.  The mask is copied on the stream. */
+kfvm_status kfvm_set_smooth_mask(kfvm_ctx* ctx, const unsigned char* mask, void* stream);
+
 /* Smooth-cell probabilities prob (device, float32 [n]) for inputs X. */
 kfvm_status kfvm_gate_forward(kfvm_ctx* ctx, const float* X, float* prob, size_t n, void* stream);
 

@@ -27,10 +27,10 @@ from functools import lru_cache
 
 import numpy as np
 
-from . import stencils
+from . import gate, stencils
 from .build import build as _build
 
-__all__ = ["Oracle", "weights", "flat_weights", "stencils", "phi_matrices", "riemann_flux", "face_points"]
+__all__ = ["Oracle", "weights", "flat_weights", "stencils", "phi_matrices", "riemann_flux", "face_points", "gate"]
 
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -52,6 +52,7 @@ class _Problem(ctypes.Structure):
         ("wts", _PD), ("gl_w", _PD),
         ("recon", _I), ("riemann", _I),
         ("positivity", _I), ("kappa", _D), ("eta", _D),
+        ("mask", ctypes.POINTER(ctypes.c_ubyte)),
     ]
 
 
@@ -173,7 +174,7 @@ class Oracle:
 
     def __init__(self, n, dim: int = 2, R: int = 2, lo=None, hi=None, bc="periodic", gamma: float = 1.4,
                  ell: float = 5.0, eps: float = 1e-40, recon: str = "weno", riemann: str = "hllc",
-                 positivity: bool = True, kappa: float = 0.1, eta: float = 0.0):
+                 positivity: bool = True, kappa: float = 0.1, eta: float = 0.0, mask=None):
         self.dim, self.R, self.nv = dim, R, dim + 2
         n = list(n) + [1] * (3 - len(n))
         lo = list(lo) if lo is not None else [0.0] * dim
@@ -211,7 +212,12 @@ class Oracle:
         pb.lin_w = _pd(self._lin_w)
         pb.nface, pb.nderiv = self.nface, self.nderiv
         pb.wts, pb.gl_w = _pd(self._wts), _pd(self._gl)
-        pb.recon = {"weno": 0, "linear": 1}[recon]
+        pb.recon = {"weno": 0, "linear": 1, "gated": 2}[recon]
+        if mask is not None:
+            self._mask = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).ravel())
+            if self._mask.size != self.ncell:
+                raise ValueError("mask needs one byte per cell")
+            pb.mask = self._mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
         pb.riemann = {"hllc": 0, "hll": 1}[riemann]
         pb.positivity, pb.kappa, pb.eta = int(bool(positivity)), float(kappa), float(eta)
         self._pb = pb

@@ -293,10 +293,12 @@ typedef struct {
   int nface, nderiv;    /* F, M */
   const double* wts;    /* per q: F*N_q face weights then M*N_q derivative weights */
   const double* gl_w;   /* R Gauss-Legendre weights on [-1/2,1/2] */
-  int recon;            /* 0: WENO-AO in linearized primitive variables; 1: linear S0, conservative */
+  int recon;            /* 0: WENO-AO in linearized primitive variables; 1: linear S0, conservative;
+                           2: per-cell choice of the two by `mask` (the gated reconstruction) */
   int riemann;          /* 0: HLLC, 1: HLL */
   int positivity;       /* 1: apply the positivity-preserving limiter of Sec. 4 to the Riemann states */
   double kappa, eta;    /* bound relaxation kappa and flattener eta of Sec. 4.1 */
+  const unsigned char* mask; /* recon 2: per cell, 1 = linear (smooth), 0 = WENO-AO */
 } kfo_problem;
 
 static long ncell_of(const kfo_problem* pb) { return (long)pb->n[0] * pb->n[1] * pb->n[2]; }
@@ -390,7 +392,7 @@ int kfo_reconstruct(const kfo_problem* pb, const double* U, double* faces, doubl
           long cl = ((long)iz * pb->n[1] + iy) * pb->n[0] + ix;
           for (int v = 0; v < nv; ++v) sten[l * nv + v] = U[v * nc + cl];
         }
-        if (pb->recon == 1) {
+        if (pb->recon == 1 || (pb->recon == 2 && pb->mask && pb->mask[c])) {
           /* unlimited linear reconstruction on S0 in conservative variables */
           const double* r0 = pb->wts;
           for (int s = 0; s < F; ++s)

@@ -65,6 +65,8 @@ def load():
     L.kfvm_gate_get_params.argtypes = [P, ctypes.POINTER(ctypes.c_float), S]
     L.kfvm_gate_features.argtypes = [P, P, P, P, D, P]
     L.kfvm_gate_forward.argtypes = [P, P, P, S, P]
+    L.kfvm_set_smooth_mask.argtypes = [P, P, P]
+    L.kfvm_gate_mask.argtypes = [P, P, P, P]
     L.kfvm_gate_train_step.argtypes = [P, P, P, S, ctypes.c_float, P, P, P]
     L.kfvm_stencil_info.argtypes = [I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
     L.kfvm_launch_count.argtypes = [P]
@@ -289,6 +291,18 @@ class KFVM:
         _check(self._L.kfvm_gate_features(self._ctx, _ptr(U), _ptr(X), _ptr(y), float(tau), _stream(stream)),
                "kfvm_gate_features")
         return X, y
+
+    def gate_mask(self, U, stream=None):
+        """The gate's smooth mask of U (uint8 per cell), as the gated step computes it."""
+        import torch
+        U = self._state(U)
+        m = torch.empty(self.shape[1:], dtype=torch.uint8, device=U.device)
+        _check(self._L.kfvm_gate_mask(self._ctx, _ptr(U), _ptr(m), _stream(stream)), "kfvm_gate_mask")
+        return m
+
+    def set_smooth_mask(self, mask, stream=None):
+        """Gated reconstruction driven by a caller-supplied uint8 CUDA mask (1 = linear)."""
+        _check(self._L.kfvm_set_smooth_mask(self._ctx, _ptr(mask), _stream(stream)), "kfvm_set_smooth_mask")
 
     def gate_forward(self, X, stream=None):
         import torch

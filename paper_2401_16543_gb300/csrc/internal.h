@@ -73,7 +73,8 @@ struct kfvm_ctx {
   kfvm::GateNet gate;
   float* d_gate = nullptr;        // float32 master parameters
   float* d_gate_adam = nullptr;   // Adam moments m, v (2 * count)
-  float* d_gate_grad = nullptr;   // gradient accumulator
+  float* d_gate_grad = nullptr;   // gradient accumulator (+1 float: the batch loss sum)
+  void* d_gate_pack = nullptr;    // BF16 working copy of the weights + float32 biases
   long long gate_step = 0;
   bool gate_loaded = false;
   // accounting and tracing
@@ -101,7 +102,10 @@ cudaError_t launch_shadow(kfvm_ctx* ctx, const double* U, float* shadow, cudaStr
 // Fused face fluxes + divergence + stage update (stage 0: write dUdt to out).
 cudaError_t launch_flux_update(kfvm_ctx* ctx, int stage, const void* faces, const double* U0, const double* Us,
                                double* out, cudaStream_t st);
-cudaError_t launch_gate_mask(kfvm_ctx* ctx, const double* U, cudaStream_t st);
+// shadow != nullptr: features from the float32 shadow (mixed path), else from U
+cudaError_t launch_gate_mask(kfvm_ctx* ctx, const double* U, const float* shadow, cudaStream_t st);
+// WENO-AO training labels of the gate (float32 shadow input).
+cudaError_t launch_labels(kfvm_ctx* ctx, const float* shadow, float* y, float thresh, cudaStream_t st);
 cudaError_t launch_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, cudaStream_t st);
 cudaError_t launch_gate_forward(kfvm_ctx* ctx, const float* X, float* prob, size_t n, cudaStream_t st);
 cudaError_t launch_gate_train(kfvm_ctx* ctx, const float* X, const float* y, size_t n, float lr, float* loss,

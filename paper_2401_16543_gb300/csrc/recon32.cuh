@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS) recon32_kernel(GridArgs a,
   };
 
   // ---- phase 1: linear cells (all cells in the linear mode) ----
-  bool weno_here = active && (mode == 0 || (mode == 2 && !gate_mask[cell]));
+  bool weno_here = active && (mode == 0 || (mode >= 2 && !gate_mask[cell]));
   if (active && !weno_here) {
     float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
     cell_ref(c, uc, ut, kin, irt);
@@ -365,6 +365,112 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS) recon32_kernel(GridArgs a,
     out4[(long long)s * ncell + cell] = make_float4(rs, uo[0], uo[1], ps);
     if (D == 3) faces[4LL * F * ncell + (long long)s * ncell + cell] = uo[D == 3 ? 2 : 0];
   }
+}
+
+// Training labels of the learned gate, from the cell's own WENO-AO weights
+// (Eqs. 22, 24, 25): y = 1 when every linearized primitive component is smooth
+// by the weights (omega_0/gamma_0 >= thresh = 1 - tau) or varies over the
+// stencil by less than 1e-6 of its scale (rho~ for density, p~ for pressure,
+// the sound speed for velocities), where WENO-AO and the linear
+// reconstruction differ by less than that; else 0.
+template <int D, int R>
+__global__ void __launch_bounds__(T32<D, R>::THREADS) label_kernel(GridArgs a, const float* __restrict__ S,
+                                                                   float* __restrict__ y, float thresh,
+                                                                   const __grid_constant__ W32<D, R> W) {
+  using G = Geo<D, R>;
+  using T = T32<D, R>;
+  constexpr int NV = G::NV, SN = T::SN, NQ = G::NQ, N0 = G::N0;
+  extern __shared__ float smem32[];
+  float* sm = smem32;
+  const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+  const float gm1 = a.gammaf - 1.0f;
+  const int tiles_x = (a.n[0] + T::TX - 1) / T::TX, tiles_y = (a.n[1] + T::TY - 1) / T::TY;
+  int b = blockIdx.x;
+  const int bx = b % tiles_x;
+  b /= tiles_x;
+  const int by = b % tiles_y;
+  const int bz = b / tiles_y;
+  const int x0 = bx * T::TX - T::H, y0 = by * T::TY - T::H, z0 = (D == 3) ? bz * T::TZ - T::H : 0;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < SN; i += T::THREADS) {
+    const int sx = i % T::SX, sy = (i / T::SX) % T::SY, sz = i / (T::SX * T::SY);
+    const int gx = map_index(x0 + sx, a.n[0], a.bc[0][0], a.bc[0][1]);
+    const int gy = map_index(y0 + sy, a.n[1], a.bc[1][0], a.bc[1][1]);
+    const int gz = (D == 3) ? map_index(z0 + sz, a.n[2], a.bc[2][0], a.bc[2][1]) : 0;
+    const long long gc = ((long long)gz * a.n[1] + gy) * a.n[0] + gx;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm[v * SN + i] = S[v * ncell + gc];
+  }
+  __syncthreads();
+  const int lx = tid % T::TX, ly = (tid / T::TX) % T::TY, lz = tid / (T::TX * T::TY);
+  const int x = bx * T::TX + lx, yy = by * T::TY + ly, z = (D == 3) ? bz * T::TZ + lz : 0;
+  if (x >= a.n[0] || yy >= a.n[1] || z >= a.n[2]) return;
+  const long long cell = ((long long)z * a.n[1] + yy) * a.n[0] + x;
+  const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (D == 3 ? lz + T::H : 0));
+  float uc[NV], ut[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int v = 0; v < NV; ++v) uc[v] = sm[v * SN + c];
+  const float irt = __frcp_rn(uc[0]);
+  float kin = 0.0f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    ut[k] = uc[1 + k] * irt;
+    kin = fmaf(ut[k], ut[k], kin);
+  }
+  kin *= 0.5f;
+  float worst = 1.0f;
+  float g[N0];
+  // component scales of the amplitude clause
+  float m2c = 0.0f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) m2c = fmaf(uc[1 + k], uc[1 + k], m2c);
+  const float pc = gm1 * fmaf(-0.5f * m2c, irt, uc[D + 1]);
+  const float cs = sqrtf(fmaxf(a.gammaf * pc * irt, 0.0f));
+#pragma unroll 1
+  for (int v = 0; v < NV; ++v) {
+    gather_row<D, R>(sm, c, v, g, uc, ut, kin, irt, gm1, std::make_integer_sequence<int, N0>{});
+    float amp = 0.0f;
+#pragma unroll
+    for (int l = 0; l < N0; ++l) amp = fmaxf(amp, fabsf(g[l]));
+    const float scale = (v == 0) ? uc[0] : (v == NV - 1 ? pc : cs);
+    if (amp <= 1e-6f * scale) continue;  // negligible variation: smooth whatever the weights say
+    float beta[NQ];
+    all_betas<D, R>(W, g, beta, std::make_integer_sequence<int, NQ>{});
+    float bmax = 0.0f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) bmax = fmaxf(bmax, beta[q]);
+    float ratio = 1.0f;
+    if (bmax > 0.0f) {
+      const float ib = __frcp_rn(bmax);
+      const float e = fmaxf(a.epsf * ib * ib, 1e-30f);
+      float om0 = 0.0f, sum = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const float bq = beta[q] * ib;
+        const float o = __fdividef((float)linear_weight<D>(q), fmaf(bq, bq, e));
+        if (q == 0) om0 = o;
+        sum += o;
+      }
+      ratio = om0 / (sum * (float)linear_weight<D>(0));
+    }
+    worst = fminf(worst, ratio);
+  }
+  y[cell] = worst >= thresh ? 1.0f : 0.0f;
+}
+
+template <int D, int R>
+cudaError_t launch_labels(kfvm_ctx* ctx, const float* shadow, float* y, float thresh, cudaStream_t st) {
+  using T = T32<D, R>;
+  using G = Geo<D, R>;
+  const GridArgs a = make_grid_args(ctx);
+  const int tiles = ((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
+                    ((D == 3) ? (ctx->n[2] + T::TZ - 1) / T::TZ : 1);
+  const size_t smem = sizeof(float) * G::NV * T::SN;
+  std::unique_ptr<W32<D, R>> wp(new W32<D, R>);
+  for (int i = 0; i < G::WCOUNT; ++i) wp->w[i] = (float)ctx->w_host[i];
+  label_kernel<D, R><<<tiles, T::THREADS, smem, st>>>(a, shadow, y, thresh, *wp);
+  ctx->launches += 1;
+  return cudaGetLastError();
 }
 
 template <int D, int R>

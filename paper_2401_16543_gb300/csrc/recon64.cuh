@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(Cfg64<D, R>::kThreads) recon64_kernel(GridArgs
     const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (D == 3 ? lz + T::H : 0));
     const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
     if (!(sm[c] > 0.0) || !(sp[c] > 0.0)) raise_flag(a.status, kFlagNonphysical);
-    const bool linear = (mode == 1) || (mode == 2 && gate_mask[cell]);
+    const bool linear = (mode == 1) || (mode >= 2 && gate_mask[cell]);
     if (linear)
       recon_cell<D, R, true>(a, W, sm, c, gs + tid, faces, cell, ncell);
     else
