@@ -166,12 +166,20 @@ def time_steps(g, U, steps, stream, flush_buf):
     return total  # ms
 
 
+GATE_PARAMS = os.path.join(ROOT, "paper_2401_16543_gb300", "gate_params_2d.npy")
+GATE_THRESHOLD = 0.8
+
+
 def make_solver(path, U_dev):
+    import numpy as np
+
     from paper_2401_16543_gb300 import KFVM
     g = KFVM([N_GRID, N_GRID], dims=2, radius=RADIUS, bc="outflow")
     if path in ("fp32", "gated"):
         g.set_option("precision", 32)
     if path == "gated":
+        g.gate_set_params(np.load(GATE_PARAMS))
+        g.set_option("gate_threshold", GATE_THRESHOLD)
         g.set_option("recon", 2)
     return g
 
@@ -195,7 +203,7 @@ def measure_path(path, U0, steps, warmup, stream, flush_buf, profile_kernel):
         g.set_option("profile", 0)
         launches = g.launches - launches0
         g.sync_status(stream)
-    return g, ms, prof, launches
+    return g, ms, prof, launches, U
 
 
 def main():
@@ -222,14 +230,14 @@ def main():
 
     path = args.path
     if path == "auto":
-        path = "fp32"
+        path = "gated" if os.path.exists(GATE_PARAMS) else "fp32"
     sampler = ClockSampler(torch.cuda.current_device() if world == 1 else local)
     sampler.start()
     # ---- headline path, resident inputs ----
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    g, ms, prof, launches = measure_path(path, U0, args.steps, args.warmup, stream, flush_buf, None)
+    g, ms, prof, launches, g_final_state = measure_path(path, U0, args.steps, args.warmup, stream, flush_buf, None)
     torch.cuda.synchronize()
     if dist is not None:
         t = torch.tensor([ms], device=dev)
@@ -239,13 +247,15 @@ def main():
     clocks = sampler.stop()
     value = world * ncell * 3 * args.steps / (ms * 1e-3)
 
-    # ---- plain FP64 path on the same workload ----
-    if path == "fp64":
-        fp64 = {"value": value, "ms_per_step": ms / args.steps}
-    else:
-        _, ms64, _, _ = measure_path("fp64", U0, max(3, args.steps // 4), 2, stream, flush_buf, None)
-        fp64 = {"value": world * ncell * 3 * max(3, args.steps // 4) / (ms64 * 1e-3),
-                "ms_per_step": ms64 / max(3, args.steps // 4)}
+    # ---- the other paths on the same workload (plain FP64 is the metric's reference) ----
+    others = {}
+    for other in ("fp64", "fp32", "gated"):
+        if other == path or (other == "gated" and not os.path.exists(GATE_PARAMS)):
+            continue
+        k = max(3, args.steps // 4)
+        _, mso, _, _, _ = measure_path(other, U0, k, 2, stream, flush_buf, None)
+        others[other] = {"value": world * ncell * 3 * k / (mso * 1e-3), "ms_per_step": mso / k, "steps": k}
+    fp64 = others.get("fp64", {"value": value, "ms_per_step": ms / args.steps})
 
     # ---- end to end through the C ABI with host buffers ----
     Uh = U0.cpu().pin_memory()
@@ -276,6 +286,16 @@ def main():
     n_launch, kms = prof.get(kern, (0, 0.0))
     mode = "weno" if path in ("fp64", "fp32") else "gated"
     flops = algo_flops_per_cell(2, RADIUS, "weno") * ncell
+    smooth_frac = None
+    if path == "gated":
+        # WENO cells at WENO cost, gated cells at the linear reconstruction's cost, averaged over
+        # the masks of the initial and the final state of the timed run
+        fr = []
+        for Us in (U0, g_final_state):
+            fr.append(float(g.gate_mask(Us).float().mean().item()))
+        smooth_frac = sum(fr) / len(fr)
+        flops = ncell * (smooth_frac * algo_flops_per_cell(2, RADIUS, "linear")
+                         + (1 - smooth_frac) * algo_flops_per_cell(2, RADIUS, "weno"))
     peak_flops = pkg.measure_fma_peak(64 if path == "fp64" else 32)
     achieved = flops / (kms / n_launch * 1e-3) if n_launch else 0.0
     traffic = None
@@ -288,7 +308,7 @@ def main():
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak_flops if peak_flops else None, "traffic": traffic,
                 "peak_source": f"measured live: FP{64 if path == 'fp64' else 32} FMA loop on every SM",
-                "algo_flops_per_cell": flops / ncell, "mode": mode,
+                "algo_flops_per_cell": flops / ncell, "mode": mode, "gated_smooth_fraction": smooth_frac,
                 "kernel_share": {k: round(v[1] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
 
     # ---- the oracle on the host cores ----
@@ -312,9 +332,12 @@ def main():
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "gated": "f32+bf16"}[path],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "radius": RADIUS, "path": path,
+                       "gate": ({"params": "paper_2401_16543_gb300/gate_params_2d.npy",
+                                 "threshold": GATE_THRESHOLD} if path == "gated" else None),
                        "l2": "flushed between timed steps (256 MB write outside the step events)",
                        "replicas": world},
             "fp64_plain": fp64,
+            "other_paths": others,
             "speedup_vs_fp64": value / fp64["value"],
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
             "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()}, "clocks": clocks,

@@ -405,7 +405,7 @@ kfvm_status kfvm_reconstruct(kfvm_ctx* ctx, const double* U, void* faces, void* 
     KFVM_LAUNCH(ctx, kProfRecon64, st, launch_recon64(ctx, U, (double*)faces, st));
   } else {
     KFVM_LAUNCH(ctx, kProfShadow, st, launch_shadow(ctx, U, ctx->d_shadow, st));
-    if (ctx->recon == 2) KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, U, ctx->d_shadow, st));
+    // the FP32 reconstruction evaluates the learned gate itself (fused)
     KFVM_LAUNCH(ctx, kProfRecon32, st, launch_recon32(ctx, U, ctx->d_shadow, (float*)faces, st));
   }
   return KFVM_OK;
@@ -438,8 +438,8 @@ kfvm_status kfvm_step(kfvm_ctx* ctx, double* U, double cfl, double t_remaining, 
   const double* in[3] = {U, ctx->d_stage, ctx->d_stage};
   double* outp[3] = {ctx->d_stage, ctx->d_stage, U};
   for (int k = 0; k < 3; ++k) {
-    if (ctx->recon == 2)
-      KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, in[k], fp32 ? ctx->d_shadow : nullptr, st));
+    if (ctx->recon == 2 && !fp32)  // the FP32 reconstruction evaluates the gate itself
+      KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, in[k], nullptr, st));
     if (fp32)
       KFVM_LAUNCH(ctx, kProfRecon32, st, launch_recon32(ctx, in[k], ctx->d_shadow, (float*)ctx->d_faces, st));
     else

@@ -22,6 +22,9 @@ struct GridArgs {
   DevScalars* scalars;
   // float32 copies for the mixed-precision kernels
   float gammaf, epsf, lo_f, hi_f;
+  // reciprocal cell sizes (host-computed: a float64 division costs ~10 FP64 issue slots here)
+  double idx[3];
+  float idxf[3];
 };
 
 inline GridArgs make_grid_args(const kfvm_ctx* c) {
@@ -44,6 +47,10 @@ inline GridArgs make_grid_args(const kfvm_ctx* c) {
   g.epsf = (float)c->eps;
   g.lo_f = (float)(1.0 - c->kappa + c->kappa * c->eta);
   g.hi_f = (float)(1.0 + c->kappa - c->kappa * c->eta);
+  for (int a = 0; a < 3; ++a) {
+    g.idx[a] = 1.0 / c->dx[a];
+    g.idxf[a] = (float)g.idx[a];
+  }
   return g;
 }
 

@@ -48,19 +48,29 @@ __global__ void __launch_bounds__(kBlock) max_rate_kernel(GridArgs a, const doub
     }
     double rate;
     if constexpr (SHADOW) {
-      // mixed-precision path: the pressure (E - |m|^2/(2 rho) cancels near vacuum) in
-      // float64, the sound speed and the rate in float32
-      const double ir = recip64(u[0]);
-      double m2 = 0.0;
+      // mixed-precision path: float32 where E/p < 8; the pressure is recovered in float64 only
+      // where E - |m|^2/(2 rho) cancels (high Mach numbers, near vacuum)
+      float uf[D + 2];
 #pragma unroll
-      for (int k = 0; k < D; ++k) m2 = fma(u[1 + k], u[1 + k], m2);
-      const double p = gm1 * fma(-0.5 * m2, ir, u[D + 1]);
-      const float cs = sqrtf((float)(a.gamma * p * ir));
-      const float irf = (float)ir;
+      for (int v = 0; v < D + 2; ++v) uf[v] = (float)u[v];
+      const float irf = __frcp_rn(uf[0]);
+      float m2f = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) m2f = fmaf(uf[1 + k], uf[1 + k], m2f);
+      float pf = (float)gm1 * fmaf(-0.5f * m2f, irf, uf[D + 1]);
+      if (!(pf > 0.125f * uf[D + 1])) {
+        const double ir = recip64(u[0]);
+        double m2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) m2 = fma(u[1 + k], u[1 + k], m2);
+        const double p = gm1 * fma(-0.5 * m2, ir, u[D + 1]);
+        pf = (p > 0.0 && u[0] > 0.0) ? (float)p : __int_as_float(0x7fc00000);
+      }
+      const float cs = sqrtf(a.gammaf * pf * irf);
       float r = 0.0f;
 #pragma unroll
-      for (int k = 0; k < D; ++k) r += (fabsf((float)u[1 + k] * irf) + cs) * (float)(1.0 / a.dx[k]);
-      rate = (p > 0.0 && u[0] > 0.0) ? (double)r : __longlong_as_double(0x7ff8000000000000LL);
+      for (int k = 0; k < D; ++k) r += (fabsf(uf[1 + k] * irf) + cs) * a.idxf[k];
+      rate = (double)r;
     } else {
       const double ir = 1.0 / u[0];
       double m2 = 0.0;
@@ -214,11 +224,11 @@ __device__ __forceinline__ bool riemann32(const float* wL, const float* wR, int 
     v2L = fmaf(wL[1 + k], wL[1 + k], v2L);
     v2R = fmaf(wR[1 + k], wR[1 + k], v2R);
   }
-  const float igm1 = 1.0f / gm1;
+  const float igm1 = __frcp_rn(gm1);
   const float EL = fmaf(pL, igm1, 0.5f * rL * v2L), ER = fmaf(pR, igm1, 0.5f * rR * v2R);
-  const float irL = 1.0f / rL, irR = 1.0f / rR;
+  const float irL = __frcp_rn(rL), irR = __frcp_rn(rR);
   const float cL = sqrtf(gamma * pL * irL), cR = sqrtf(gamma * pR * irR);
-  const float sL = sqrtf(rL), sR = sqrtf(rR), isum = 1.0f / (sL + sR);
+  const float sL = sqrtf(rL), sR = sqrtf(rR), isum = __frcp_rn(sL + sR);
   float ut2 = 0.0f, utn = 0.0f;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -262,23 +272,23 @@ __device__ __forceinline__ bool riemann32(const float* wL, const float* wR, int 
     return true;
   }
   if (solver == 1) {
-    const float idn = 1.0f / (SR - SL);
+    const float idn = __frcp_rn(SR - SL);
 #pragma unroll
     for (int v = 0; v < NV; ++v) f[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) * idn;
     return true;
   }
-  const float Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) / (rL * (SL - unL) - rR * (SR - unR));
+  const float Ss = __fdividef(pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR), rL * (SL - unL) - rR * (SR - unR));
   const bool left = Ss >= 0.0f;
   const float* uK = left ? UL : UR;
   const float* wK = left ? wL : wR;
   const float* FK = left ? FL : FR;
   const float SK = left ? SL : SR, rK = left ? rL : rR, unK = left ? unL : unR, pK = left ? pL : pR;
-  const float fac = rK * (SK - unK) / (SK - Ss);
+  const float fac = __fdividef(rK * (SK - unK), SK - Ss);
   float us[NV];
   us[0] = fac;
 #pragma unroll
   for (int k = 0; k < D; ++k) us[1 + k] = fac * (k == dir ? Ss : wK[1 + k]);
-  us[NV - 1] = fac * (uK[NV - 1] / rK + (Ss - unK) * (Ss + pK / (rK * (SK - unK))));
+  us[NV - 1] = fac * (uK[NV - 1] * (left ? irL : irR) + (Ss - unK) * (Ss + __fdividef(pK, rK * (SK - unK))));
 #pragma unroll
   for (int v = 0; v < NV; ++v) f[v] = FK[v] + SK * (us[v] - uK[v]);
   return true;
@@ -460,7 +470,7 @@ __global__ void __launch_bounds__(FTile<D>::THREADS) flux_update_kernel(GridArgs
     int lh[3] = {l[0], l[1], l[2]};
     lh[d] += 1;
     const int ilo = T::idx(d, l[0], l[1], l[2]), ihi = T::idx(d, lh[0], lh[1], lh[2]);
-    const Real idx = Real(1.0 / a.dx[d]);
+    const Real idx = sizeof(Real) == 8 ? Real(a.idx[d]) : Real(a.idxf[d]);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       Lv[v] = fma(sflux[v][ilo], idx, Lv[v]);
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(kBlock) update_kernel(GridArgs a, FluxLayout L
     const long long stride = d == 0 ? 1 : (d == 1 ? e[0] : (long long)e[0] * e[1]);
     const long long fhi = flo + stride;
     const long long nf = L.nface[d];
-    const double idx = 1.0 / a.dx[d];
+    const double idx = a.idx[d];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double lo = (double)flux[L.off[d] + v * nf + flo];
@@ -789,6 +799,8 @@ extern "C" kfvm_status kfvm_flux_static(const kfvm_grid* grid, int dims, int rad
     a.n[d] = used ? grid->n[d] : 1;
     if (a.n[d] < 1 || (used && !(grid->hi[d] > grid->lo[d]))) return KFVM_ERR_ARG;
     a.dx[d] = used ? (grid->hi[d] - grid->lo[d]) / grid->n[d] : 1.0;
+    a.idx[d] = 1.0 / a.dx[d];
+    a.idxf[d] = (float)a.idx[d];
     for (int s = 0; s < 2; ++s) {
       a.bc[d][s] = used ? grid->bc[d][s] : KFVM_BC_PERIODIC;
       if (a.bc[d][s] != KFVM_BC_PERIODIC && a.bc[d][s] != KFVM_BC_OUTFLOW) return KFVM_ERR_ARG;

@@ -16,8 +16,9 @@
 //     linearized primitive values: p_s = pi_s - (gamma-1) rho~^2 |du_s|^2 / (2 rho_s),
 //     and the positivity limiter (Sec. 4) works on the same quantities
 //     (the blend toward the cell average is linear, so it is a scaling of dW);
-//   * only the central pressure p~ is recovered in float64 (E - |m|^2/(2 rho)
-//     cancels near vacuum), with a float32 reciprocal refined by one Newton step.
+//   * the central pressure p~ is recovered in float64 (with a float32 reciprocal
+//     refined by one Newton step) wherever E/p >= 8, i.e. where E - |m|^2/(2 rho)
+//     cancels (high Mach numbers, near vacuum); elsewhere float32 suffices.
 // Output: float32 primitive (rho, u, [v, w,] p) Riemann states.
 // In the gated mode the cells the gate marks smooth take the linear S0
 // reconstruction; the others are compacted within the CTA so that whole warps
@@ -29,6 +30,7 @@
 #include <utility>
 
 #include "common.cuh"
+#include "gate.cuh"
 
 namespace kfvm {
 namespace r32 {
@@ -61,6 +63,40 @@ template <int D, int R, int L>
 struct Dlt {
   static constexpr int v = Geo<D, R>::tab.off[L][0] +
                            T32<D, R>::SX * (Geo<D, R>::tab.off[L][1] + T32<D, R>::SY * Geo<D, R>::tab.off[L][2]);
+};
+
+// offsets of the radius-2 stencil (the gate's input) in the tile of radius R
+template <int D, int R, int L>
+struct Dlt2 {
+  static constexpr int v = Geo<D, 2>::tab.off[L][0] +
+                           T32<D, R>::SX * (Geo<D, 2>::tab.off[L][1] + T32<D, R>::SY * Geo<D, 2>::tab.off[L][2]);
+};
+
+template <int D, int R, int... Ls>
+__device__ __forceinline__ void gate_features_tile(const float* __restrict__ sm, const float* __restrict__ sp, int c,
+                                                   float* f, std::integer_sequence<int, Ls...>) {
+  constexpr int N0 = Geo<D, 2>::N0;
+  ((f[Ls] = sm[c + Dlt2<D, R, Ls>::v]), ...);
+  ((f[N0 + Ls] = sp[c + Dlt2<D, R, Ls>::v]), ...);
+  gate::normalise_block<N0, Geo<D, 2>::center()>(f);
+  gate::normalise_block<N0, Geo<D, 2>::center()>(f + N0);
+}
+
+// dynamic shared memory of recon32_kernel (floats), and where the gate's pieces sit
+template <int D, int R>
+struct Smem32 {
+  using T = T32<D, R>;
+  using G = Geo<D, R>;
+  static constexpr int base = (G::NV + 1) * T::SN + G::F * G::NV * T::THREADS + T::THREADS;  // + list (ints)
+  static constexpr int pack_off = (base + 3) / 4 * 4;                                           // 16-byte aligned
+  static constexpr int pack_floats = (int)(sizeof(gate::Pack<D>) / 4);
+  static constexpr int total_gate = pack_off + pack_floats;
+  // the gate's input rows and logits live in the dW region, which phase 1 writes only after them
+  static constexpr int dw_off = (G::NV + 1) * T::SN;
+  static constexpr int xs_off = (dw_off + 3) / 4 * 4;
+  static constexpr int xs_floats = T::THREADS * gate::Dims<D>::LDX / 2;
+  static constexpr int z_off = xs_off + xs_floats;
+  static_assert(z_off + T::THREADS <= dw_off + G::F * G::NV * T::THREADS, "gate staging must fit in dW");
 };
 
 template <int D, int R>
@@ -147,11 +183,13 @@ __device__ __forceinline__ void gather_row(const float* __restrict__ sm, int c, 
 }
 
 template <int D, int R>
-__global__ void __launch_bounds__(T32<D, R>::THREADS) recon32_kernel(GridArgs a, int mode,
+__global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1) recon32_kernel(GridArgs a, int mode,
                                                                      const double* __restrict__ U,
                                                                      const float* __restrict__ S,
                                                                      float* __restrict__ faces,
                                                                      const unsigned char* __restrict__ gate_mask,
+                                                                     const gate::Pack<D>* __restrict__ gpack,
+                                                                     float zthresh,
                                                                      const __grid_constant__ W32<D, R> W) {
   using G = Geo<D, R>;
   using T = T32<D, R>;
@@ -200,6 +238,36 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS) recon32_kernel(GridArgs a,
   const long long cell = active ? ((long long)z * a.n[1] + y) * a.n[0] + x : 0;
   const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (D == 3 ? lz + T::H : 0));
   float* mydw = dw + tid;
+
+  // ---- learned gate, fused: features from the tile, the MLP on the tensor cores per warp ----
+  bool smooth = false;
+  if (mode == 2) {
+    using SM = Smem32<D, R>;
+    using DM = gate::Dims<D>;
+    gate::Pack<D>* P = reinterpret_cast<gate::Pack<D>*>(smem32 + SM::pack_off);
+    __nv_bfloat16* xs_all = reinterpret_cast<__nv_bfloat16*>(smem32 + SM::xs_off);
+    float* zs = smem32 + SM::z_off;
+    gate::load_pack<D>(gpack, P);
+    float f[DM::NIN];
+    gate_features_tile<D, R>(sm, sp, c, f, std::make_integer_sequence<int, Geo<D, 2>::N0>{});
+    const int warp = tid >> 5, lane = tid & 31;
+    __nv_bfloat16* xs = xs_all + warp * 32 * DM::LDX;
+#pragma unroll
+    for (int k = 0; k < DM::KIN; ++k) xs[lane * DM::LDX + k] = __float2bfloat16_rn(k < DM::NIN ? f[k] : 0.0f);
+    __syncthreads();  // pack and rows in place
+    float h1[2][4][4], h2[2][4][4], zf[2][4];
+    gate::forward32<D>(*P, xs, h1, h2, zf);
+    if ((lane & 3) == 0) {
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        zs[warp * 32 + 16 * mt + (lane >> 2)] = zf[mt][0];
+        zs[warp * 32 + 16 * mt + (lane >> 2) + 8] = zf[mt][2];
+      }
+    }
+    __syncwarp();
+    smooth = zs[tid] > zthresh;
+    __syncthreads();  // the dW region is reused from here on
+  }
   constexpr auto SEQ_L = std::make_integer_sequence<int, N0>{};
   constexpr auto SEQ_S = std::make_integer_sequence<int, F>{};
 
@@ -218,7 +286,7 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS) recon32_kernel(GridArgs a,
   };
 
   // ---- phase 1: linear cells (all cells in the linear mode) ----
-  bool weno_here = active && (mode == 0 || (mode >= 2 && !gate_mask[cell]));
+  bool weno_here = active && (mode == 0 || (mode == 2 && !smooth) || (mode == 3 && !gate_mask[cell]));
   if (active && !weno_here) {
     float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
     cell_ref(c, uc, ut, kin, irt);
@@ -236,48 +304,54 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS) recon32_kernel(GridArgs a,
     if (weno_here) list[atomicAdd(&s_count, 1)] = tid;
   }
   __syncthreads();
-  const int nweno = (mode == 0) ? TH : s_count;
-  for (int k = tid; k < nweno; k += TH) {
-    const int owner = (mode == 0) ? k : list[k];
-    if (mode == 0 && !active) continue;
+  // one WENO-AO reconstruction variable of one cell (the variables are independent)
+  auto weno_var = [&](int owner, int v) {
     const int olx = owner % T::TX, oly = (owner / T::TX) % T::TY, olz = owner / (T::TX * T::TY);
     const int oc = (olx + T::H) + T::SX * ((oly + T::H) + T::SY * (D == 3 ? olz + T::H : 0));
-    float* odw = dw + owner;
     float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
     cell_ref(oc, uc, ut, kin, irt);
     float g[N0];
-#pragma unroll 1
-    for (int v = 0; v < NV; ++v) {
-      gather_row<D, R>(sm, oc, v, g, uc, ut, kin, irt, gm1, SEQ_L);
-      float beta[NQ];
-      all_betas<D, R>(W, g, beta, std::make_integer_sequence<int, NQ>{});
-      float bmax = 0.0f;
+    gather_row<D, R>(sm, oc, v, g, uc, ut, kin, irt, gm1, SEQ_L);
+    float beta[NQ];
+    all_betas<D, R>(W, g, beta, std::make_integer_sequence<int, NQ>{});
+    float bmax = 0.0f;
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) bmax = fmaxf(bmax, beta[q]);
-      float coef[NQ];
-      if (bmax > 0.0f) {
-        const float ib = __frcp_rn(bmax);
-        const float e = fmaxf(a.epsf * ib * ib, 1e-30f);
-        float om[NQ], sum = 0.0f;
+    for (int q = 0; q < NQ; ++q) bmax = fmaxf(bmax, beta[q]);
+    float coef[NQ];
+    if (bmax > 0.0f) {
+      const float ib = __frcp_rn(bmax);
+      const float e = fmaxf(a.epsf * ib * ib, 1e-30f);
+      float om[NQ], sum = 0.0f;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const float bq = beta[q] * ib;
-          om[q] = __fdividef((float)linear_weight<D>(q), fmaf(bq, bq, e));
-          sum += om[q];
-        }
-        const float inv = __frcp_rn(sum);
-        const float w0 = om[0] * inv;
-        coef[0] = w0 / (float)linear_weight<D>(0);
-#pragma unroll
-        for (int q = 1; q < NQ; ++q)
-          coef[q] = fmaf(-w0, (float)(linear_weight<D>(q) / linear_weight<D>(0)), om[q] * inv);
-      } else {
-        coef[0] = 1.0f;
-#pragma unroll
-        for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
+      for (int q = 0; q < NQ; ++q) {
+        const float bq = beta[q] * ib;
+        om[q] = __fdividef((float)linear_weight<D>(q), fmaf(bq, bq, e));
+        sum += om[q];
       }
-      all_faces_weno<D, R>(W, g, coef, odw + v * TH, NV * TH, SEQ_S);
+      const float inv = __frcp_rn(sum);
+      const float w0 = om[0] * inv;
+      coef[0] = w0 / (float)linear_weight<D>(0);
+#pragma unroll
+      for (int q = 1; q < NQ; ++q)
+        coef[q] = fmaf(-w0, (float)(linear_weight<D>(q) / linear_weight<D>(0)), om[q] * inv);
+    } else {
+      coef[0] = 1.0f;
+#pragma unroll
+      for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
     }
+    all_faces_weno<D, R>(W, g, coef, dw + owner + v * TH, NV * TH, SEQ_S);
+  };
+  if (mode == 0) {
+    // every active cell is a WENO cell: each thread its own cell, variable by variable
+    if (active) {
+#pragma unroll 1
+      for (int v = 0; v < NV; ++v) weno_var(tid, v);
+    }
+  } else {
+    // compacted WENO cells, one (cell, variable) pair per thread so that several warps share them
+    const int npairs = s_count * NV;
+#pragma unroll 1
+    for (int k = tid; k < npairs; k += TH) weno_var(list[k / NV], k % NV);
   }
   __syncthreads();
   if (!active) return;
@@ -285,8 +359,10 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS) recon32_kernel(GridArgs a,
   // ---- tail: central pressure in float64, limiter, primitive Riemann states ----
   float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
   cell_ref(c, uc, ut, kin, irt);
-  float pt;
-  {
+  // central pressure: float32 where E/p < 8 (the cancellation E - |m|^2/(2 rho) then costs
+  // under 3 bits, relative error below 6e-7), else recovered in float64 from the state
+  float pt = sp[c];
+  if (!(pt > 0.125f * uc[D + 1])) {
     double m2 = 0.0, u8[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) u8[v] = U[v * ncell + cell];
@@ -480,13 +556,18 @@ cudaError_t launch(kfvm_ctx* ctx, const double* U, const float* shadow, float* f
   const GridArgs a = make_grid_args(ctx);
   const int tiles = ((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
                     ((D == 3) ? (ctx->n[2] + T::TZ - 1) / T::TZ : 1);
-  const size_t smem = sizeof(float) * ((G::NV + 1) * T::SN + G::F * G::NV * T::THREADS) + sizeof(int) * T::THREADS;
+  const bool learned = ctx->recon == 2;
+  const size_t smem = sizeof(float) * (learned ? Smem32<D, R>::total_gate : Smem32<D, R>::base);
   auto kern = recon32_kernel<D, R>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float) * Smem32<D, R>::total_gate));
   if (e != cudaSuccess) return e;
   std::unique_ptr<W32<D, R>> wp(new W32<D, R>);
   for (int i = 0; i < G::WCOUNT; ++i) wp->w[i] = (float)ctx->w_host[i];
-  kern<<<tiles, T::THREADS, smem, st>>>(a, ctx->recon, U, shadow, faces, ctx->d_gate_mask, *wp);
+  const float th = (float)ctx->gate_threshold;
+  const float zth = logf(th / (1.0f - th));
+  kern<<<tiles, T::THREADS, smem, st>>>(a, ctx->recon, U, shadow, faces, ctx->d_gate_mask,
+                                        (const gate::Pack<D>*)ctx->d_gate_pack, zth, *wp);
   ctx->launches += 1;
   return cudaGetLastError();
 }
