@@ -286,7 +286,21 @@ kfvm_status kfvm_init(kfvm_ctx** out, const kfvm_grid* g, int dims, int radius, 
   }
   if (e == cudaSuccess) e = dalloc(&c->d_w64, c->wcount);
   if (e == cudaSuccess) e = dalloc(&c->d_w32, c->wcount);
-  if (e == cudaSuccess) e = dalloc((double**)&c->d_faces, (size_t)F * nv * nc);
+  // Riemann-state buffer: the whole grid if it fits in 8 GiB (float64), else 3D z-slabs
+  // of S planes plus one plane on each side (kfvm_step loops over the slabs)
+  {
+    const size_t plane = (size_t)F * nv * c->n[0] * c->n[1] * sizeof(double);
+    const size_t budget = (size_t)8 << 30;
+    if (dims == 2 || plane * c->n[2] <= budget) {
+      c->slab_planes = c->n[2];
+      c->face_planes = c->n[2];
+    } else {
+      const long long s = (long long)(budget / plane) - 2;
+      c->slab_planes = (int)(s < 1 ? 1 : (s > c->n[2] ? c->n[2] : s));
+      c->face_planes = c->slab_planes + 2;
+    }
+  }
+  if (e == cudaSuccess) e = dalloc((double**)&c->d_faces, (size_t)F * nv * c->n[0] * c->n[1] * c->face_planes);
   if (e == cudaSuccess) e = dalloc(&c->d_flux, flux_total);
   if (e == cudaSuccess) e = dalloc(&c->d_stage, nv * nc);
   if (e == cudaSuccess) e = dalloc(&c->d_shadow, nv * nc);
@@ -315,6 +329,8 @@ void kfvm_destroy(kfvm_ctx* c) {
   cudaFree(c->d_faces);
   cudaFree(c->d_flux);
   cudaFree(c->d_stage);
+  cudaFree(c->d_stage2);
+  cudaFree(c->d_shadow2);
   cudaFree(c->d_L);
   cudaFree(c->d_shadow);
   cudaFree(c->d_gate_mask);
@@ -383,6 +399,11 @@ kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double v) {
   } else if (k == "eps") {
     if (!(v > 0)) return KFVM_ERR_ARG;
     ctx->eps = v;
+  } else if (k == "slab_planes") {
+    // split 3D steps into z-slabs of this many planes (at most what the buffer was sized for)
+    if (!(v >= 1) || ctx->dims != 3) return KFVM_ERR_ARG;
+    const int limit = ctx->face_planes == ctx->n[2] ? ctx->n[2] : ctx->face_planes - 2;
+    ctx->slab_planes = (int)v < limit ? (int)v : limit;
   } else if (k == "profile") {
     if (v != 0 && v != 1) return KFVM_ERR_ARG;
     ctx->profile = (int)v;
@@ -420,31 +441,80 @@ kfvm_status kfvm_flux(kfvm_ctx* ctx, const void* faces, double* dUdt, void* stre
   return KFVM_OK;
 }
 
+namespace {
+
+// One RK stage (or, with stage 0, dUdt) over the grid, in z-slabs when the step was sized for them:
+// Riemann states of the planes zc_lo - 1 .. zc_hi (wrapped or skipped at the ends), then the fused
+// flux divergence / stage update of the planes zc_lo .. zc_hi - 1.
+kfvm_status stage_pass(kfvm_ctx* ctx, int stage, const double* in, const double* U0, double* out,
+                       const float* shadow_in, float* shadow_out, cudaStream_t st) {
+  const bool fp32 = ctx->precision == 32;
+  const int nz = ctx->n[2], S = ctx->slab_planes;
+  const bool multi = ctx->dims == 3 && S < nz;
+  for (int z0 = 0; z0 < (multi ? nz : 1); z0 += (multi ? S : 1)) {
+    const int zc_lo = multi ? z0 : 0, zc_hi = multi ? (z0 + S < nz ? z0 + S : nz) : 0;
+    const int zf_first = multi ? z0 - 1 : 0, zf_count = multi ? zc_hi - zc_lo + 2 : 0;
+    if (fp32)
+      KFVM_LAUNCH(ctx, kProfRecon32, st,
+                  launch_recon32(ctx, in, shadow_in, (float*)ctx->d_faces, st, zf_first, zf_count));
+    else
+      KFVM_LAUNCH(ctx, kProfRecon64, st, launch_recon64(ctx, in, (double*)ctx->d_faces, st, zf_first, zf_count));
+    KFVM_LAUNCH(ctx, kProfUpdate, st,
+                launch_flux_update(ctx, stage, ctx->d_faces, U0, in, out, st, shadow_out, zc_lo, zc_hi, zf_first,
+                                   zf_count));
+  }
+  return KFVM_OK;
+}
+
+kfvm_status ensure_slab_buffers(kfvm_ctx* ctx) {
+  if (!(ctx->dims == 3 && ctx->slab_planes < ctx->n[2])) return KFVM_OK;
+  const size_t n = (size_t)ctx->nv * ctx->ncell;
+  if (!ctx->d_stage2) KFVM_TRY(cudaMalloc(&ctx->d_stage2, sizeof(double) * n));
+  if (!ctx->d_shadow2) KFVM_TRY(cudaMalloc(&ctx->d_shadow2, sizeof(float) * n));
+  return KFVM_OK;
+}
+
+}  // namespace
+
 kfvm_status kfvm_rhs(kfvm_ctx* ctx, const double* U, double* dUdt, void* stream) {
-  kfvm_status s = kfvm_reconstruct(ctx, U, ctx ? ctx->d_faces : nullptr, stream);
+  kfvm_status s = check_ready(ctx);
   if (s) return s;
-  return kfvm_flux(ctx, ctx->d_faces, dUdt, stream);
+  if (!U || !dUdt) return KFVM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ctx->precision == 64) {
+    if (ctx->recon == 2) KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, U, nullptr, st));
+  } else {
+    KFVM_LAUNCH(ctx, kProfShadow, st, launch_shadow(ctx, U, ctx->d_shadow, st));
+  }
+  return stage_pass(ctx, 0, U, nullptr, dUdt, ctx->d_shadow, nullptr, st);
 }
 
 kfvm_status kfvm_step(kfvm_ctx* ctx, double* U, double cfl, double t_remaining, double* dt_out, void* stream) {
   kfvm_status s = check_ready(ctx);
   if (s) return s;
   if (!U || !(cfl > 0) || !(t_remaining > 0)) return KFVM_ERR_ARG;
-  if (U == ctx->d_stage) return KFVM_ERR_ARG;
+  if (U == ctx->d_stage || U == ctx->d_stage2) return KFVM_ERR_ARG;
+  s = ensure_slab_buffers(ctx);
+  if (s) return s;
   cudaStream_t st = (cudaStream_t)stream;
   const bool fp32 = ctx->precision == 32;
+  const bool multi = ctx->dims == 3 && ctx->slab_planes < ctx->n[2];
   // dt from U (and, in the FP32 mode, the float32 shadow of U for the first stage)
   KFVM_LAUNCH(ctx, kProfMaxRate, st, launch_max_rate(ctx, U, cfl, t_remaining, st));
-  const double* in[3] = {U, ctx->d_stage, ctx->d_stage};
-  double* outp[3] = {ctx->d_stage, ctx->d_stage, U};
+  // Shu-Osher stages; with slabs no stage writes the state its own reconstruction still reads
+  double* A = ctx->d_stage;
+  double* B = multi ? ctx->d_stage2 : ctx->d_stage;
+  float* s0 = ctx->d_shadow;
+  float* s1 = multi ? ctx->d_shadow2 : ctx->d_shadow;
+  const double* in[3] = {U, A, B};
+  double* outp[3] = {A, B, U};
+  const float* sh_in[3] = {s0, s1, s0};
+  float* sh_out[3] = {s1, s0, nullptr};
   for (int k = 0; k < 3; ++k) {
     if (ctx->recon == 2 && !fp32)  // the FP32 reconstruction evaluates the gate itself
       KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, in[k], nullptr, st));
-    if (fp32)
-      KFVM_LAUNCH(ctx, kProfRecon32, st, launch_recon32(ctx, in[k], ctx->d_shadow, (float*)ctx->d_faces, st));
-    else
-      KFVM_LAUNCH(ctx, kProfRecon64, st, launch_recon64(ctx, in[k], (double*)ctx->d_faces, st));
-    KFVM_LAUNCH(ctx, kProfUpdate, st, launch_flux_update(ctx, k + 1, ctx->d_faces, U, in[k], outp[k], st));
+    s = stage_pass(ctx, k + 1, in[k], U, outp[k], sh_in[k], sh_out[k], st);
+    if (s) return s;
   }
   if (dt_out) {
     KFVM_TRY(cudaMemcpyAsync(dt_out, &ctx->d_scalars->dt, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -25,6 +25,9 @@ struct GridArgs {
   // reciprocal cell sizes (host-computed: a float64 division costs ~10 FP64 issue slots here)
   double idx[3];
   float idxf[3];
+  // slabs (3D): the Riemann-state buffer holds the z-planes zf_first .. zf_first + zf_count - 1
+  // (wrapped periodically); a launch processes the cells of planes zc_lo .. zc_hi - 1
+  int zf_first, zf_count, zc_lo, zc_hi;
 };
 
 inline GridArgs make_grid_args(const kfvm_ctx* c) {
@@ -51,7 +54,31 @@ inline GridArgs make_grid_args(const kfvm_ctx* c) {
     g.idx[a] = 1.0 / c->dx[a];
     g.idxf[a] = (float)g.idx[a];
   }
+  g.zf_first = 0;
+  g.zf_count = c->n[2];
+  g.zc_lo = 0;
+  g.zc_hi = c->n[2];
   return g;
+}
+
+// Index of grid cell (x, y, z) in the Riemann-state buffer (see zf_first / zf_count).
+__device__ __forceinline__ long long face_cell(const GridArgs& a, int x, int y, int z) {
+  // z is a wrapped grid index; the buffer's planes run from zf_first (possibly -1) upwards
+  int l = z - a.zf_first;
+  if (l < 0) l += a.n[2];
+  if (l >= a.zf_count) l -= a.n[2];
+  return ((long long)l * a.n[1] + y) * a.n[0] + x;
+}
+__device__ __forceinline__ long long face_ncell(const GridArgs& a) {
+  return (long long)a.zf_count * a.n[0] * a.n[1];
+}
+// Global z of plane l of the Riemann-state buffer, or -1 when that plane lies
+// outside a non-periodic grid.
+__device__ __forceinline__ int slab_plane(const GridArgs& a, int l) {
+  int z = a.zf_first + l;
+  if (z >= 0 && z < a.n[2]) return z;
+  if (a.bc[2][0] != KFVM_BC_PERIODIC) return -1;
+  return ((z % a.n[2]) + a.n[2]) % a.n[2];
 }
 
 // Ghost-cell index map (Sec. 5.3 step 1): periodic wraps, outflow clamps.

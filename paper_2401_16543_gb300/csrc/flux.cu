@@ -342,8 +342,10 @@ __device__ __forceinline__ bool face_flux_at(const GridArgs& a, const Real* __re
   if (i == nd) {
     if (a.bc[dir][1] == KFVM_BC_PERIODIC) cr[dir] = 0; else { has_r = false; cr[dir] = nd - 1; }
   }
-  const long long lcell = ((long long)cl[2] * a.n[1] + cl[1]) * a.n[0] + cl[0];
-  const long long rcell = ((long long)cr[2] * a.n[1] + cr[1]) * a.n[0] + cr[0];
+  // positions in the Riemann-state buffer (which may hold a slab of z-planes)
+  const long long lcell = face_cell(a, cl[0], cl[1], cl[2]);
+  const long long rcell = face_cell(a, cr[0], cr[1], cr[2]);
+  ncell = face_ncell(a);
   constexpr double w2[2] = {0.5, 0.5};
   constexpr double w3[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
 #pragma unroll
@@ -435,9 +437,10 @@ __global__ void __launch_bounds__(FTile<D>::THREADS) flux_update_kernel(GridArgs
   const int bz = b / tiles_y;
   const int tid = threadIdx.x;
   const int l[3] = {tid % T::TX, (tid / T::TX) % T::TY, tid / (T::TX * T::TY)};
-  const int c[3] = {bx * T::TX + l[0], by * T::TY + l[1], (D == 3) ? bz * T::TZ + l[2] : 0};
-  const bool active = c[0] < a.n[0] && c[1] < a.n[1] && c[2] < a.n[2];
+  const int c[3] = {bx * T::TX + l[0], by * T::TY + l[1], (D == 3) ? a.zc_lo + bz * T::TZ + l[2] : 0};
+  const bool active = c[0] < a.n[0] && c[1] < a.n[1] && c[2] < (D == 3 ? a.zc_hi : 1);
   const int tdim[3] = {T::TX, T::TY, T::TZ};
+  const int last[3] = {a.n[0] - 1, a.n[1] - 1, (D == 3 ? a.zc_hi : 1) - 1};
   if (active) {
     bool ok = true;
 #pragma unroll
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(FTile<D>::THREADS) flux_update_kernel(GridArgs
       const int i0 = T::idx(d, l[0], l[1], l[2]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) sflux[v][i0] = f[v];
-      if (l[d] == tdim[d] - 1 || c[d] == a.n[d] - 1) {
+      if (l[d] == tdim[d] - 1 || c[d] == last[d]) {
         int ch[3] = {c[0], c[1], c[2]}, lh[3] = {l[0], l[1], l[2]};
         ch[d] += 1;
         lh[d] += 1;
@@ -589,18 +592,26 @@ cudaError_t face_flux_dr(kfvm_ctx* ctx, const void* faces, cudaStream_t st) {
 
 template <int D, int R>
 cudaError_t flux_update_dr(kfvm_ctx* ctx, int stage, const void* faces, const double* U0, const double* Us,
-                           double* out, cudaStream_t st) {
+                           double* out, cudaStream_t st, float* shadow_out, int zc_lo, int zc_hi, int zf_first,
+                           int zf_count) {
   using T = FTile<D>;
-  const GridArgs a = make_grid_args(ctx);
+  GridArgs a = make_grid_args(ctx);
+  if (D == 3 && zc_hi > 0) {
+    a.zc_lo = zc_lo;
+    a.zc_hi = zc_hi;
+    a.zf_first = zf_first;
+    a.zf_count = zf_count;
+  }
   const unsigned tiles = (unsigned)(((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
-                                    ((D == 3) ? (ctx->n[2] + T::TZ - 1) / T::TZ : 1));
+                                    ((D == 3) ? (a.zc_hi - a.zc_lo + T::TZ - 1) / T::TZ : 1));
   const bool shadow = ctx->precision == 32 && stage >= 1 && stage <= 2;
+  if (!shadow_out) shadow_out = ctx->d_shadow;
   if (ctx->precision == 64)
     flux_update_kernel<D, R, double, false><<<tiles, T::THREADS, 0, st>>>(a, (const double*)faces, stage, U0, Us, out,
                                                                          nullptr);
   else if (shadow)
     flux_update_kernel<D, R, float, true><<<tiles, T::THREADS, 0, st>>>(a, (const float*)faces, stage, U0, Us, out,
-                                                                       ctx->d_shadow);
+                                                                       shadow_out);
   else
     flux_update_kernel<D, R, float, false><<<tiles, T::THREADS, 0, st>>>(a, (const float*)faces, stage, U0, Us, out,
                                                                         nullptr);
@@ -714,11 +725,13 @@ cudaError_t launch_update(kfvm_ctx* ctx, int stage, const double* U0, const doub
 }
 
 cudaError_t launch_flux_update(kfvm_ctx* ctx, int stage, const void* faces, const double* U0, const double* Us,
-                               double* out, cudaStream_t st) {
-  if (ctx->dims == 2 && ctx->R == 2) return flux_update_dr<2, 2>(ctx, stage, faces, U0, Us, out, st);
-  if (ctx->dims == 2 && ctx->R == 3) return flux_update_dr<2, 3>(ctx, stage, faces, U0, Us, out, st);
-  if (ctx->dims == 3 && ctx->R == 2) return flux_update_dr<3, 2>(ctx, stage, faces, U0, Us, out, st);
-  return flux_update_dr<3, 3>(ctx, stage, faces, U0, Us, out, st);
+                               double* out, cudaStream_t st, float* shadow_out, int zc_lo, int zc_hi, int zf_first,
+                               int zf_count) {
+  if (ctx->dims == 2 && ctx->R == 2) return flux_update_dr<2, 2>(ctx, stage, faces, U0, Us, out, st, shadow_out, 0, 0, 0, 0);
+  if (ctx->dims == 2 && ctx->R == 3) return flux_update_dr<2, 3>(ctx, stage, faces, U0, Us, out, st, shadow_out, 0, 0, 0, 0);
+  if (ctx->dims == 3 && ctx->R == 2)
+    return flux_update_dr<3, 2>(ctx, stage, faces, U0, Us, out, st, shadow_out, zc_lo, zc_hi, zf_first, zf_count);
+  return flux_update_dr<3, 3>(ctx, stage, faces, U0, Us, out, st, shadow_out, zc_lo, zc_hi, zf_first, zf_count);
 }
 
 cudaError_t fma_peak(int bits, double* flops) {
@@ -823,6 +836,10 @@ extern "C" kfvm_status kfvm_flux_static(const kfvm_grid* grid, int dims, int rad
   a.riemann = riemann;
   a.status = status;
   a.scalars = nullptr;
+  a.zf_first = 0;
+  a.zf_count = a.n[2];
+  a.zc_lo = 0;
+  a.zc_hi = a.n[2];
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return KFVM_ERR_CUDA;
   cudaError_t e;

@@ -64,6 +64,10 @@ struct kfvm_ctx {
   double* d_flux = nullptr;      // face-averaged fluxes, per direction nv * (n_d + 1) * prod(n_other)
   size_t flux_off[3] = {0, 0, 0};
   double* d_stage = nullptr;     // one intermediate RK state, nv * ncell
+  double* d_stage2 = nullptr;    // second intermediate state (only when the step runs in z-slabs)
+  float* d_shadow2 = nullptr;    // second float32 shadow (slabs)
+  int slab_planes = 1;           // z-planes per slab; = n[2] for a single slab
+  int face_planes = 1;           // z-planes the Riemann-state buffer can hold
   double* d_L = nullptr;         // optional dUdt scratch for kfvm_rhs-style calls
   float* d_shadow = nullptr;     // float32 copy of the state for the FP32 path, nv * ncell
   unsigned char* d_gate_mask = nullptr;  // per cell: 1 = smooth (linear), 0 = WENO
@@ -93,15 +97,21 @@ namespace kfvm {
 // of kernels it launched to ctx->launches.
 cudaError_t launch_build_weights(kfvm_ctx* ctx, cudaStream_t st, int* d_err);
 cudaError_t launch_max_rate(kfvm_ctx* ctx, const double* U, double cfl, double t_rem, cudaStream_t st);
-cudaError_t launch_recon64(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_t st);
-cudaError_t launch_recon32(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st);
+// zf_first / zf_count select the z-planes whose Riemann states go to `faces` (3D slabs);
+// zf_count = 0 means the whole grid.
+cudaError_t launch_recon64(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_t st, int zf_first = 0,
+                           int zf_count = 0);
+cudaError_t launch_recon32(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st,
+                           int zf_first = 0, int zf_count = 0);
 cudaError_t launch_face_flux(kfvm_ctx* ctx, const void* faces, cudaStream_t st);
 // stage: 0 -> dUdt only (to out), 1/2/3 -> SSP-RK3 stages writing the new state to out.
 cudaError_t launch_update(kfvm_ctx* ctx, int stage, const double* U0, const double* Us, double* out, cudaStream_t st);
 cudaError_t launch_shadow(kfvm_ctx* ctx, const double* U, float* shadow, cudaStream_t st);
 // Fused face fluxes + divergence + stage update (stage 0: write dUdt to out).
+// zc_lo..zc_hi: planes of cells to update (zc_hi = 0: all); the faces hold planes zf_first.. (slabs).
 cudaError_t launch_flux_update(kfvm_ctx* ctx, int stage, const void* faces, const double* U0, const double* Us,
-                               double* out, cudaStream_t st);
+                               double* out, cudaStream_t st, float* shadow_out = nullptr, int zc_lo = 0,
+                               int zc_hi = 0, int zf_first = 0, int zf_count = 0);
 // shadow != nullptr: features from the float32 shadow (mixed path), else from U
 cudaError_t launch_gate_mask(kfvm_ctx* ctx, const double* U, const float* shadow, cudaStream_t st);
 // WENO-AO training labels of the gate (float32 shadow input).

@@ -209,9 +209,10 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
   b /= tiles_x;
   const int by = b % tiles_y;
   const int bz = b / tiles_y;
-  const int x0 = bx * T::TX - T::H, y0 = by * T::TY - T::H, z0 = (D == 3) ? bz * T::TZ - T::H : 0;
+  const int x0 = bx * T::TX - T::H, y0 = by * T::TY - T::H, z0 = (D == 3) ? a.zf_first + bz * T::TZ - T::H : 0;
   const int tid = threadIdx.x;
   if (tid == 0) s_count = 0;
+  const long long ncell_f = face_ncell(a);
 
   for (int i = tid; i < SN; i += TH) {
     const int sx = i % T::SX, sy = (i / T::SX) % T::SY, sz = i / (T::SX * T::SY);
@@ -233,9 +234,11 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
   __syncthreads();
 
   const int lx = tid % T::TX, ly = (tid / T::TX) % T::TY, lz = tid / (T::TX * T::TY);
-  const int x = bx * T::TX + lx, y = by * T::TY + ly, z = (D == 3) ? bz * T::TZ + lz : 0;
-  const bool active = x < a.n[0] && y < a.n[1] && z < a.n[2];
+  const int x = bx * T::TX + lx, y = by * T::TY + ly, l = (D == 3) ? bz * T::TZ + lz : 0;
+  const int z = (D == 3) ? (l < a.zf_count ? slab_plane(a, l) : -1) : 0;
+  const bool active = x < a.n[0] && y < a.n[1] && z >= 0;
   const long long cell = active ? ((long long)z * a.n[1] + y) * a.n[0] + x : 0;
+  const long long fcell = active ? ((long long)l * a.n[1] + y) * a.n[0] + x : 0;
   const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (D == 3 ? lz + T::H : 0));
   float* mydw = dw + tid;
 
@@ -438,8 +441,8 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
     const float dp = sc * mydw[(s * NV + NV - 1) * TH];
     const float ps = fmaf(-cq * du2, irs, pt + dp);
     // float32 layout: [s][cell] float4 (rho, u, v, p), then (3D) the plane [s][cell] of w
-    out4[(long long)s * ncell + cell] = make_float4(rs, uo[0], uo[1], ps);
-    if (D == 3) faces[4LL * F * ncell + (long long)s * ncell + cell] = uo[D == 3 ? 2 : 0];
+    out4[(long long)s * ncell_f + fcell] = make_float4(rs, uo[0], uo[1], ps);
+    if (D == 3) faces[4LL * F * ncell_f + (long long)s * ncell_f + fcell] = uo[D == 3 ? 2 : 0];
   }
 }
 
@@ -550,12 +553,17 @@ cudaError_t launch_labels(kfvm_ctx* ctx, const float* shadow, float* y, float th
 }
 
 template <int D, int R>
-cudaError_t launch(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st) {
+cudaError_t launch(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st,
+                   int zf_first, int zf_count) {
   using T = T32<D, R>;
   using G = Geo<D, R>;
-  const GridArgs a = make_grid_args(ctx);
+  GridArgs a = make_grid_args(ctx);
+  if (D == 3 && zf_count > 0) {
+    a.zf_first = zf_first;
+    a.zf_count = zf_count;
+  }
   const int tiles = ((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
-                    ((D == 3) ? (ctx->n[2] + T::TZ - 1) / T::TZ : 1);
+                    ((D == 3) ? (a.zf_count + T::TZ - 1) / T::TZ : 1);
   const bool learned = ctx->recon == 2;
   const size_t smem = sizeof(float) * (learned ? Smem32<D, R>::total_gate : Smem32<D, R>::base);
   auto kern = recon32_kernel<D, R>;

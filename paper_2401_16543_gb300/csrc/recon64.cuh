@@ -319,8 +319,9 @@ __global__ void __launch_bounds__(Cfg64<D, R>::kThreads) recon64_kernel(GridArgs
   b /= tiles_x;
   const int by = b % tiles_y;
   const int bz = b / tiles_y;
-  const int x0 = bx * T::TX - T::H, y0 = by * T::TY - T::H, z0 = (D == 3) ? bz * T::TZ - T::H : 0;
+  const int x0 = bx * T::TX - T::H, y0 = by * T::TY - T::H, z0 = (D == 3) ? a.zf_first + bz * T::TZ - T::H : 0;
   const int tid = threadIdx.x;
+  const long long ncell_f = face_ncell(a);
 
   for (int i = tid; i < SN; i += TS) {
     const int sx = i % T::SX, sy = (i / T::SX) % T::SY, sz = i / (T::SX * T::SY);
@@ -341,22 +342,25 @@ __global__ void __launch_bounds__(Cfg64<D, R>::kThreads) recon64_kernel(GridArgs
   const WFun<D, R, P> W{wglob, wpar};
   for (int lc = tid; lc < T::THREADS; lc += TS) {
     const int lx = lc % T::TX, ly = (lc / T::TX) % T::TY, lz = lc / (T::TX * T::TY);
-    const int x = bx * T::TX + lx, y = by * T::TY + ly, z = (D == 3) ? bz * T::TZ + lz : 0;
-    if (x >= a.n[0] || y >= a.n[1] || z >= a.n[2]) continue;
+    const int x = bx * T::TX + lx, y = by * T::TY + ly, l = (D == 3) ? bz * T::TZ + lz : 0;
+    if (x >= a.n[0] || y >= a.n[1] || l >= a.zf_count) continue;
+    const int z = (D == 3) ? slab_plane(a, l) : 0;
+    if (z < 0) continue;
     const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (D == 3 ? lz + T::H : 0));
     const long long cell = ((long long)z * a.n[1] + y) * a.n[0] + x;
+    const long long fc = ((long long)l * a.n[1] + y) * a.n[0] + x;
     if (!(sm[c] > 0.0) || !(sp[c] > 0.0)) raise_flag(a.status, kFlagNonphysical);
     const bool linear = (mode == 1) || (mode >= 2 && gate_mask[cell]);
     if (linear)
-      recon_cell<D, R, true>(a, W, sm, c, gs + tid, faces, cell, ncell);
+      recon_cell<D, R, true>(a, W, sm, c, gs + tid, faces, fc, ncell_f);
     else
-      recon_cell<D, R, false>(a, W, sm, c, gs + tid, faces, cell, ncell);
-    if (a.positivity) limit_cell<D, R>(a, sm, sp, c, faces, cell, ncell);
+      recon_cell<D, R, false>(a, W, sm, c, gs + tid, faces, fc, ncell_f);
+    if (a.positivity) limit_cell<D, R>(a, sm, sp, c, faces, fc, ncell_f);
   }
 }
 
 template <int D, int R>
-cudaError_t launch_dr(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_t st) {
+cudaError_t launch_dr(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_t st, int zf_first, int zf_count) {
   using T = Tile<D, R>;
   constexpr bool P = params_fit<D, R>();
   constexpr int TS = Cfg64<D, R>::kThreads;
@@ -369,9 +373,11 @@ cudaError_t launch_dr(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_
     if (e != cudaSuccess) return e;
     plan_ready[dev] = true;
   }
-  const GridArgs a = make_grid_args(ctx);
+  GridArgs a = make_grid_args(ctx);
+  a.zf_first = zf_first;
+  a.zf_count = zf_count;
   const int tiles = ((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
-                    ((D == 3) ? (ctx->n[2] + T::TZ - 1) / T::TZ : 1);
+                    ((D == 3) ? (zf_count + T::TZ - 1) / T::TZ : 1);
   const size_t smem = sizeof(double) * ((Geo<D, R>::NV + 1) * T::SN + Geo<D, R>::N0 * TS);
   auto kern = recon64_kernel<D, R, P>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -3,7 +3,8 @@
 #include "recon64.cuh"
 
 namespace kfvm {
-cudaError_t launch_recon64_32(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_t st) {
-  return r64::launch_dr<3, 2>(ctx, U, faces, st);
+cudaError_t launch_recon64_32(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_t st, int zf_first,
+                              int zf_count) {
+  return r64::launch_dr<3, 2>(ctx, U, faces, st, zf_first, zf_count);
 }
 }  // namespace kfvm
