@@ -285,7 +285,9 @@ kfvm_status kfvm_init(kfvm_ctx** out, const kfvm_grid* g, int dims, int radius, 
     flux_total += nv * faces;
   }
   if (e == cudaSuccess) e = dalloc(&c->d_w64, c->wcount);
-  if (e == cudaSuccess) e = dalloc(&c->d_w32, c->wcount);
+  // float32 weights: the packed table, or for d = 3, R = 3 the padded row table of recon32_33
+  if (e == cudaSuccess)
+    e = dalloc(&c->d_w32, (dims == 3 && radius == 3) ? recon33_table_floats() : c->wcount);
   // Riemann-state buffer: the whole grid if it fits in 8 GiB (float64), else 3D z-slabs
   // of S planes plus one plane on each side (kfvm_step loops over the slabs)
   {
@@ -361,9 +363,13 @@ kfvm_status kfvm_build_weights(kfvm_ctx* ctx, void* stream) {
   if (herr) return KFVM_ERR_SINGULAR;
   ctx->w_host.assign(ctx->wcount, 0.0);
   KFVM_TRY(cudaMemcpy(ctx->w_host.data(), ctx->d_w64, sizeof(double) * ctx->wcount, cudaMemcpyDeviceToHost));
-  std::vector<float> w32(ctx->wcount);
-  for (size_t i = 0; i < ctx->wcount; ++i) w32[i] = (float)ctx->w_host[i];
-  KFVM_TRY(cudaMemcpy(ctx->d_w32, w32.data(), sizeof(float) * ctx->wcount, cudaMemcpyHostToDevice));
+  const bool rows = ctx->dims == 3 && ctx->R == 3;
+  std::vector<float> w32(rows ? recon33_table_floats() : ctx->wcount);
+  if (rows)
+    recon33_fill_table(ctx->w_host.data(), w32.data());
+  else
+    for (size_t i = 0; i < ctx->wcount; ++i) w32[i] = (float)ctx->w_host[i];
+  KFVM_TRY(cudaMemcpy(ctx->d_w32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
   ctx->weights_built = true;
   return KFVM_OK;
 }

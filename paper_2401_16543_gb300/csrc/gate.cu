@@ -483,7 +483,6 @@ kfvm_status kfvm_gate_get_params(kfvm_ctx* ctx, float* host, size_t count) {
 kfvm_status kfvm_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, void* stream) {
   if (!ctx || !U || !X || !y || !(tau >= 0 && tau < 1)) return KFVM_ERR_ARG;
   if (!ctx->weights_built) return KFVM_ERR_STATE;
-  if (ctx->dims == 3 && ctx->R == 3) return KFVM_ERR_ARG;
   return launch_gate_features(ctx, U, X, y, tau, (cudaStream_t)stream) == cudaSuccess ? KFVM_OK : KFVM_ERR_CUDA;
 }
 

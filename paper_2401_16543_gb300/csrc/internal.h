@@ -101,6 +101,9 @@ cudaError_t launch_max_rate(kfvm_ctx* ctx, const double* U, double cfl, double t
 // zf_count = 0 means the whole grid.
 cudaError_t launch_recon64(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_t st, int zf_first = 0,
                            int zf_count = 0);
+// d = 3, R = 3 FP32 weights: padded row table (floats) and its fill from the float64 tables
+size_t recon33_table_floats();
+void recon33_fill_table(const double* w, float* out);
 cudaError_t launch_recon32(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st,
                            int zf_first = 0, int zf_count = 0);
 cudaError_t launch_face_flux(kfvm_ctx* ctx, const void* faces, cudaStream_t st);

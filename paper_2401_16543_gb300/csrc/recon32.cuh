@@ -45,6 +45,14 @@ struct T32 {
   static constexpr int SN = SX * SY * SZ;
   static constexpr int THREADS = TX * TY * TZ;
 };
+// d = 3, R = 3: an 8 x 4 x 4 tile keeps the radius-3 halo at 1400 cells
+template <>
+struct T32<3, 3> {
+  static constexpr int TX = 8, TY = 4, TZ = 4, H = 3;
+  static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SZ = TZ + 2 * H;
+  static constexpr int SN = SX * SY * SZ;
+  static constexpr int THREADS = TX * TY * TZ;
+};
 
 // compile-time views of the stencil tables (scalar constexpr members are usable in device code)
 template <int D, int R, int Q, int J>
@@ -182,6 +190,121 @@ __device__ __forceinline__ void gather_row(const float* __restrict__ sm, int c, 
   }
 }
 
+// reference state of a tile cell: averages, velocity, kinetic energy per mass, 1/rho
+template <int D, int R>
+__device__ __forceinline__ void cell_ref(const float* __restrict__ sm, int cc, float* uc, float* ut, float& kin,
+                                         float& irt) {
+  constexpr int NV = D + 2, SN = T32<D, R>::SN;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) uc[v] = sm[v * SN + cc];
+  irt = __frcp_rn(uc[0]);
+  kin = 0.0f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    ut[k] = uc[1 + k] * irt;
+    kin = fmaf(ut[k], ut[k], kin);
+  }
+  kin *= 0.5f;
+}
+
+// Tail of the FP32 reconstruction of one cell: central pressure (float64 where E/p shows
+// cancellation), positivity limiter (Sec. 4) on the reconstructed dW = dwget(s, v), and the
+// float32 primitive Riemann states.
+template <int D, int R, class DW>
+__device__ __forceinline__ void write_states(const GridArgs& a, const float* __restrict__ sm,
+                                             const float* __restrict__ sp, int c, const double* __restrict__ U,
+                                             long long ncell, long long cell, long long fcell, long long ncell_f,
+                                             float* faces, DW dwget) {
+  using G = Geo<D, R>;
+  using T = T32<D, R>;
+  constexpr int NV = G::NV, F = G::F;
+  const float gm1 = a.gammaf - 1.0f;
+  float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
+  cell_ref<D, R>(sm, c, uc, ut, kin, irt);
+  // central pressure: float32 where E/p < 8 (the cancellation E - |m|^2/(2 rho) then costs
+  // under 3 bits, relative error below 6e-7), else recovered in float64 from the state
+  float pt = sp[c];
+  if (!(pt > 0.125f * uc[D + 1])) {
+    double m2 = 0.0, u8[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u8[v] = U[v * ncell + cell];
+#pragma unroll
+    for (int k = 0; k < D; ++k) m2 = fma(u8[1 + k], u8[1 + k], m2);
+    const double p8 = (a.gamma - 1.0) * fma(-0.5 * m2, recip64(u8[0]), u8[D + 1]);
+    pt = (float)p8;
+    if (!(u8[0] > 0.0) || !(p8 > 0.0)) raise_flag(a.status, kFlagNonphysical);
+  }
+  const float rt = uc[0];
+  const float cq = 0.5f * gm1 * rt * rt;  // (gamma-1) rho~^2 / 2
+  float th = 1.0f, thp = 1.0f;
+  if (a.positivity) {
+    float rmax = -3.0e38f, rmin = 3.0e38f, pmin = 3.0e38f;
+#pragma unroll
+    for (int k = (D == 3 ? -1 : 0); k <= (D == 3 ? 1 : 0); ++k)
+#pragma unroll
+      for (int j = -1; j <= 1; ++j)
+#pragma unroll
+        for (int i = -1; i <= 1; ++i) {
+          const int o = c + i + T::SX * (j + T::SY * k);
+          rmax = fmaxf(rmax, sm[o]);
+          rmin = fminf(rmin, sm[o]);
+          pmin = fminf(pmin, sp[o]);
+        }
+    const float rho_max = rmax * a.hi_f, rho_min = rmin * a.lo_f, p_min = pmin * a.lo_f;
+#pragma unroll
+    for (int s = 0; s < F; ++s) {
+      const float drs = dwget(s, 0);
+      const float rs = rt + drs;
+      if (rs < rho_min) th = fminf(th, (rt - rho_min) / (rt - rs));
+      if (rs > rho_max) th = fminf(th, (rho_max - rt) / (rs - rt));
+    }
+    // p(theta) >= p_min  <=>  (pt + theta dpi - p_min) (rt + theta drho) >= cq theta^2 |du|^2
+    auto admissible = [&](float t, float dr, float dp, float du2) {
+      const float rr = fmaf(t, dr, rt);
+      return rr > 0.0f && (fmaf(t, dp, pt) - p_min) * rr >= cq * t * t * du2;
+    };
+#pragma unroll 1
+    for (int s = 0; s < F; ++s) {
+      const float dr = th * dwget(s, 0);
+      const float dp = th * dwget(s, NV - 1);
+      float du2 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float du = th * dwget(s, 1 + k);
+        du2 = fmaf(du, du, du2);
+      }
+      if (admissible(1.0f, dr, dp, du2)) continue;
+      float lo = 0.0f, hi = 1.0f;
+#pragma unroll 1
+      for (int it = 0; it < 40; ++it) {
+        const float mid = 0.5f * (lo + hi);
+        if (admissible(mid, dr, dp, du2)) lo = mid; else hi = mid;
+      }
+      thp = fminf(thp, lo);
+    }
+  }
+  const float sc = th * thp;
+  float4* out4 = reinterpret_cast<float4*>(faces);
+#pragma unroll 1
+  for (int s = 0; s < F; ++s) {
+    const float dr = sc * dwget(s, 0);
+    const float rs = rt + dr;
+    const float irs = __frcp_rn(rs);
+    float du2 = 0.0f, uo[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float du = sc * dwget(s, 1 + k);
+      du2 = fmaf(du, du, du2);
+      uo[k] = fmaf(rt * du, irs, ut[k]);
+    }
+    const float dp = sc * dwget(s, NV - 1);
+    const float ps = fmaf(-cq * du2, irs, pt + dp);
+    // float32 layout: [s][cell] float4 (rho, u, v, p), then (3D) the plane [s][cell] of w
+    out4[(long long)s * ncell_f + fcell] = make_float4(rs, uo[0], uo[1], ps);
+    if (D == 3) faces[4LL * F * ncell_f + (long long)s * ncell_f + fcell] = uo[D == 3 ? 2 : 0];
+  }
+}
+
 template <int D, int R>
 __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1) recon32_kernel(GridArgs a, int mode,
                                                                      const double* __restrict__ U,
@@ -274,25 +397,12 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
   constexpr auto SEQ_L = std::make_integer_sequence<int, N0>{};
   constexpr auto SEQ_S = std::make_integer_sequence<int, F>{};
 
-  // reference state of the cell
-  auto cell_ref = [&](int cc, float* uc, float* ut, float& kin, float& irt) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) uc[v] = sm[v * SN + cc];
-    irt = __frcp_rn(uc[0]);
-    kin = 0.0f;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      ut[k] = uc[1 + k] * irt;
-      kin = fmaf(ut[k], ut[k], kin);
-    }
-    kin *= 0.5f;
-  };
 
   // ---- phase 1: linear cells (all cells in the linear mode) ----
   bool weno_here = active && (mode == 0 || (mode == 2 && !smooth) || (mode == 3 && !gate_mask[cell]));
   if (active && !weno_here) {
     float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
-    cell_ref(c, uc, ut, kin, irt);
+    cell_ref<D, R>(sm, c, uc, ut, kin, irt);
     float g[N0];
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) {
@@ -312,7 +422,7 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
     const int olx = owner % T::TX, oly = (owner / T::TX) % T::TY, olz = owner / (T::TX * T::TY);
     const int oc = (olx + T::H) + T::SX * ((oly + T::H) + T::SY * (D == 3 ? olz + T::H : 0));
     float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
-    cell_ref(oc, uc, ut, kin, irt);
+    cell_ref<D, R>(sm, oc, uc, ut, kin, irt);
     float g[N0];
     gather_row<D, R>(sm, oc, v, g, uc, ut, kin, irt, gm1, SEQ_L);
     float beta[NQ];
@@ -360,90 +470,8 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
   if (!active) return;
 
   // ---- tail: central pressure in float64, limiter, primitive Riemann states ----
-  float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
-  cell_ref(c, uc, ut, kin, irt);
-  // central pressure: float32 where E/p < 8 (the cancellation E - |m|^2/(2 rho) then costs
-  // under 3 bits, relative error below 6e-7), else recovered in float64 from the state
-  float pt = sp[c];
-  if (!(pt > 0.125f * uc[D + 1])) {
-    double m2 = 0.0, u8[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) u8[v] = U[v * ncell + cell];
-#pragma unroll
-    for (int k = 0; k < D; ++k) m2 = fma(u8[1 + k], u8[1 + k], m2);
-    const double p8 = (a.gamma - 1.0) * fma(-0.5 * m2, recip64(u8[0]), u8[D + 1]);
-    pt = (float)p8;
-    if (!(u8[0] > 0.0) || !(p8 > 0.0)) raise_flag(a.status, kFlagNonphysical);
-  }
-  const float rt = uc[0];
-  const float cq = 0.5f * gm1 * rt * rt;  // (gamma-1) rho~^2 / 2
-  float th = 1.0f, thp = 1.0f;
-  if (a.positivity) {
-    float rmax = -3.0e38f, rmin = 3.0e38f, pmin = 3.0e38f;
-#pragma unroll
-    for (int k = (D == 3 ? -1 : 0); k <= (D == 3 ? 1 : 0); ++k)
-#pragma unroll
-      for (int j = -1; j <= 1; ++j)
-#pragma unroll
-        for (int i = -1; i <= 1; ++i) {
-          const int o = c + i + T::SX * (j + T::SY * k);
-          rmax = fmaxf(rmax, sm[o]);
-          rmin = fminf(rmin, sm[o]);
-          pmin = fminf(pmin, sp[o]);
-        }
-    const float rho_max = rmax * a.hi_f, rho_min = rmin * a.lo_f, p_min = pmin * a.lo_f;
-#pragma unroll
-    for (int s = 0; s < F; ++s) {
-      const float drs = mydw[(s * NV) * TH];
-      const float rs = rt + drs;
-      if (rs < rho_min) th = fminf(th, (rt - rho_min) / (rt - rs));
-      if (rs > rho_max) th = fminf(th, (rho_max - rt) / (rs - rt));
-    }
-    // p(theta) >= p_min  <=>  (pt + theta dpi - p_min) (rt + theta drho) >= cq theta^2 |du|^2
-    auto admissible = [&](float t, float dr, float dp, float du2) {
-      const float rr = fmaf(t, dr, rt);
-      return rr > 0.0f && (fmaf(t, dp, pt) - p_min) * rr >= cq * t * t * du2;
-    };
-#pragma unroll 1
-    for (int s = 0; s < F; ++s) {
-      const float dr = th * mydw[(s * NV) * TH];
-      const float dp = th * mydw[(s * NV + NV - 1) * TH];
-      float du2 = 0.0f;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const float du = th * mydw[(s * NV + 1 + k) * TH];
-        du2 = fmaf(du, du, du2);
-      }
-      if (admissible(1.0f, dr, dp, du2)) continue;
-      float lo = 0.0f, hi = 1.0f;
-#pragma unroll 1
-      for (int it = 0; it < 40; ++it) {
-        const float mid = 0.5f * (lo + hi);
-        if (admissible(mid, dr, dp, du2)) lo = mid; else hi = mid;
-      }
-      thp = fminf(thp, lo);
-    }
-  }
-  const float sc = th * thp;
-  float4* out4 = reinterpret_cast<float4*>(faces);
-#pragma unroll 1
-  for (int s = 0; s < F; ++s) {
-    const float dr = sc * mydw[(s * NV) * TH];
-    const float rs = rt + dr;
-    const float irs = __frcp_rn(rs);
-    float du2 = 0.0f, uo[3];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const float du = sc * mydw[(s * NV + 1 + k) * TH];
-      du2 = fmaf(du, du, du2);
-      uo[k] = fmaf(rt * du, irs, ut[k]);
-    }
-    const float dp = sc * mydw[(s * NV + NV - 1) * TH];
-    const float ps = fmaf(-cq * du2, irs, pt + dp);
-    // float32 layout: [s][cell] float4 (rho, u, v, p), then (3D) the plane [s][cell] of w
-    out4[(long long)s * ncell_f + fcell] = make_float4(rs, uo[0], uo[1], ps);
-    if (D == 3) faces[4LL * F * ncell_f + (long long)s * ncell_f + fcell] = uo[D == 3 ? 2 : 0];
-  }
+  write_states<D, R>(a, sm, sp, c, U, ncell, cell, fcell, ncell_f, faces,
+                     [&](int s, int v) { return mydw[(s * NV + v) * TH]; });
 }
 
 // Training labels of the learned gate, from the cell's own WENO-AO weights

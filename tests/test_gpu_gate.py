@@ -172,3 +172,49 @@ def test_learned_mask_matches_oracle_gate(kfvm, precision):
     far = np.abs(pr - 0.5) > 1e-2
     assert far.mean() > 0.9
     assert np.array_equal(mask[far] == 1, pr[far] > 0.5)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_gated_reconstruction_3d_r3_with_a_given_mask(kfvm, precision):
+    """3D, radius 3 (the float32 row-table kernel): a mixed linear/WENO mask against the oracle."""
+    n = (10, 9, 6)
+    U0 = workloads.mixed_voronoi(3, 10, 6, seed=17)[:, :n[2], :n[1], :n[0]].contiguous()
+    Xr = ogate.features(U0.numpy(), 3, "outflow")
+    mask = (np.abs(Xr[:, :33]).max(axis=1) < 0.99).astype(np.uint8)
+    mask[::5] = 1 - mask[::5]
+    ref = oracle.Oracle(list(n), dim=3, R=3, bc="outflow", recon="gated", mask=mask)
+    g = kfvm.KFVM(list(n), dims=3, radius=3, bc="outflow")
+    g.set_option("precision", precision)
+    g.set_smooth_mask(torch.from_numpy(mask).cuda())
+    U = U0.cuda()
+    U1r, _ = ref.step(U0.numpy(), 0.4)
+    g.step(U, 0.4)
+    err = np.abs(U.cpu().numpy() - U1r).max() / np.abs(U1r).max()
+    assert err <= (1e-12 if precision == 64 else 2e-6), err
+
+
+@pytest.mark.parametrize("dim,R,n", [(2, 2, (40, 24)), (3, 2, (12, 9, 8)), (3, 3, (12, 9, 8))])
+def test_fused_gate_decisions_equal_gate_mask(kfvm, dim, R, n):
+    """The FP32 reconstruction's fused gate takes the decisions kfvm_gate_mask reports: its Riemann
+    states equal those of a reconstruction driven by that mask, up to cells at the threshold.
+    (A full step differs, since the fused gate re-decides on every stage's state.)"""
+    m = max(n)
+    U0 = workloads.mixed_voronoi(dim, m, 8, seed=19)
+    U0 = (U0[:, :n[2], :n[1], :n[0]] if dim == 3 else U0[:, :n[1], :n[0]]).contiguous()
+    g = kfvm.KFVM(list(n), dims=dim, radius=R, bc="outflow")
+    g.set_option("precision", 32)
+    g.gate_set_params(ogate.init_params(dim, seed=43))
+    g.set_option("recon", 2)
+    # threshold at the median probability, so that both branches are exercised
+    X, _ = g.gate_features(U0.cuda(), 0.5)
+    th = float(g.gate_forward(X).median().item())
+    g.set_option("gate_threshold", min(max(th, 0.02), 0.98))
+    mask = g.gate_mask(U0.cuda())
+    assert 0.05 < mask.float().mean().item() < 0.95
+    f2 = g.faces_primitive(g.reconstruct(U0.cuda())).cpu().numpy()
+    h = kfvm.KFVM(list(n), dims=dim, radius=R, bc="outflow")
+    h.set_option("precision", 32)
+    h.set_smooth_mask(mask)
+    f3 = h.faces_primitive(h.reconstruct(U0.cuda())).cpu().numpy()
+    d = np.abs(f2 - f3).max(axis=(0, 1))
+    assert (d > 0).mean() <= 0.01, (d > 0).mean()

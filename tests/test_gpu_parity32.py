@@ -47,7 +47,7 @@ def _state(dim, n, seed):
 
 
 CASES = [(2, 2, (40, 24), "outflow"), (2, 3, (45, 17), "outflow"), (3, 2, (13, 10, 7), "periodic"),
-         (2, 2, (37, 19), "periodic")]
+         (2, 2, (37, 19), "periodic"), (3, 3, (10, 9, 6), "outflow"), (3, 3, (9, 8, 7), "periodic")]
 
 
 @pytest.mark.parametrize("dim,R,n,bc", CASES)
