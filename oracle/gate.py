@@ -8,8 +8,13 @@ module states, in plain FP64 numpy, what the GPU's gate computes:
 * ``features``: for each cell, the radius-2 full stencil of rho and of the
   cell-average pressure p = (gamma-1)(E - |m|^2/(2 rho)), each block as
   deviations from the central cell's value divided by
-  max(max |deviation|, 1e-6 |central value|) (+1e-30): exactly zero on
-  constant data, unchanged by a common scaling of the state.
+  d = max(max |deviation|, 1e-5 |central value|) (+1e-30): exactly zero on
+  constant data, unchanged by a common scaling of the state (the 1e-5 floor keeps
+  the ~1e-7 rounding of a float32 pressure below 0.05 in a flat block).  In 3D two more
+  inputs describe the shell 4 < |o|^2 <= 9 that a radius-3 reconstruction also
+  reads (the radius-2 block cannot see a jump three cells away): per block
+  m / (m + d) with m = max |deviation| over the shell, in [0, 1); they are zero
+  unless the reconstruction radius is 3.
 * ``labels``: 1 when every linearized primitive component is smooth by the
   cell's own WENO-AO weights (omega_0/gamma_0 >= 1 - tau; Eqs. 24-25 of the
   paper, from the oracle's reconstruction) or varies over the radius-R stencil
@@ -34,7 +39,13 @@ H = 32
 
 
 def n_in(dim: int) -> int:
-    return 2 * len(stencils.full_stencil(dim, 2))
+    return 2 * len(stencils.full_stencil(dim, 2)) + (2 if dim == 3 else 0)
+
+
+def shell_offsets():
+    """3D offsets with 4 < |o|^2 <= 9: the radius-3 stencil minus the radius-2 stencil."""
+    inner = set(map(tuple, stencils.full_stencil(3, 2)))
+    return [o for o in stencils.full_stencil(3, 3) if tuple(o) not in inner]
 
 
 def param_count(dim: int) -> int:
@@ -78,8 +89,9 @@ def bf16(x):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def features(U, dim: int, bc="periodic", gamma: float = 1.4) -> np.ndarray:
-    """Gate inputs of every cell, [ncell, NIN] (cells in x-fastest order)."""
+def features(U, dim: int, bc="periodic", gamma: float = 1.4, R: int = 2) -> np.ndarray:
+    """Gate inputs of every cell, [ncell, NIN] (cells in x-fastest order); R is the
+    reconstruction radius (3D shell inputs are computed for R = 3, zero otherwise)."""
     U = np.asarray(U, dtype=np.float64)
     if isinstance(bc, str):
         bc = [bc] * dim
@@ -87,37 +99,45 @@ def features(U, dim: int, bc="periodic", gamma: float = 1.4) -> np.ndarray:
     shape = U.shape[1:]
     mode = ["wrap" if b == "periodic" else "edge" for b in bc]
     # numpy axes are (z,) y, x: axis a of the grid is numpy axis dim-1-a
+    H = 3  # halo wide enough for the 3D shell
     padded = []
     for v in range(dim + 2):
         a = U[v]
         for ax in range(dim):
             npax = dim - 1 - ax
             widths = [(0, 0)] * dim
-            widths[npax] = (2, 2)
+            widths[npax] = (H, H)
             a = np.pad(a, widths, mode=mode[ax])
         padded.append(a)
     P = np.stack(padded)
     rho = P[0]
     m2 = sum(P[1 + k] ** 2 for k in range(dim))
     p = (gamma - 1.0) * (P[dim + 1] - 0.5 * m2 / rho)
-    cols_r, cols_p = [], []
-    for o in s0:
+
+    def column(field, o):
         sl = []
         for npax in range(dim):
             ax = dim - 1 - npax
-            lo = 2 + o[ax]
+            lo = H + o[ax]
             sl.append(slice(lo, lo + shape[npax]))
-        cols_r.append(rho[tuple(sl)].ravel())
-        cols_p.append(p[tuple(sl)].ravel())
+        return field[tuple(sl)].ravel()
+
     centre = [n for n, o in enumerate(s0) if o == (0, 0, 0)][0]
-    out = []
-    for cols in (cols_r, cols_p):
-        A = np.stack(cols, axis=1)
+    out, shell = [], []
+    for field in (rho, p):
+        A = np.stack([column(field, o) for o in s0], axis=1)
         c = A[:, centre:centre + 1]
         dev = A - c
-        scale = np.maximum(np.abs(dev).max(axis=1, keepdims=True), 1e-6 * np.abs(c) + 1e-30)
+        scale = np.maximum(np.abs(dev).max(axis=1, keepdims=True), 1e-5 * np.abs(c) + 1e-30)
         out.append(dev / scale)
-    return np.concatenate(out, axis=1)
+        if dim == 3:
+            if R >= 3:
+                Sh = np.stack([column(field, o) for o in shell_offsets()], axis=1)
+                m = np.abs(Sh - c).max(axis=1, keepdims=True)
+                shell.append(m / (m + scale))
+            else:
+                shell.append(np.zeros_like(c))
+    return np.concatenate(out + shell, axis=1)
 
 
 def linprim_amplitude(U, dim: int, R: int, bc="periodic", gamma: float = 1.4):

@@ -285,7 +285,7 @@ class KFVM:
     def gate_features(self, U, tau: float = 0.02, stream=None):
         import torch
         U = self._state(U)
-        n_in = 2 * (13 if self.dims == 2 else 33)
+        n_in = 26 if self.dims == 2 else 68  # radius-2 blocks of rho and p (+ 3D radius-3 shell inputs)
         X = torch.empty((self.ncell, n_in), dtype=torch.float32, device=U.device)
         y = torch.empty(self.ncell, dtype=torch.float32, device=U.device)
         _check(self._L.kfvm_gate_features(self._ctx, _ptr(U), _ptr(X), _ptr(y), float(tau), _stream(stream)),

@@ -10,7 +10,7 @@
 //
 // Network: NIN -> 32 -> 32 -> 1 (ReLU, ReLU, sigmoid).  Input: the radius-2
 // full stencil of rho and of the cell-average pressure, each as deviations from
-// the central cell divided by max(max |deviation|, 1e-6 |central value|), so a
+// the central cell divided by max(max |deviation|, 1e-5 |central value|), so a
 // feature vector describes the shape of the data and not its amplitude (as the
 // WENO weights do) and is exactly zero on constant data in any precision.  Matrix products run on the tensor cores with
 // mma.sync.m16n8k16 (BF16 operands, FP32 accumulation) on 32-row warp tiles;
@@ -29,16 +29,19 @@
 namespace kfvm {
 namespace gate {
 
+__constant__ ShellTable c_shell = make_shell();
+
 template <int D, int L>
 struct Off2 {
   static constexpr int x = Geo<D, 2>::tab.off[L][0], y = Geo<D, 2>::tab.off[L][1], z = Geo<D, 2>::tab.off[L][2];
 };
 
 // Gate features of cell (x, y, z) from the state (float64, or its float32
-// shadow on the mixed-precision path), written to f[NIN].
+// shadow on the mixed-precision path), written to f[NIN]; in 3D the two shell
+// inputs are computed when `shell` (radius-3 reconstruction), else zero.
 template <int D, typename TU, int... Ls>
 __device__ __forceinline__ void features(const GridArgs& a, const TU* __restrict__ U, long long ncell, int x,
-                                         int y, int z, float* f, std::integer_sequence<int, Ls...>) {
+                                         int y, int z, float* f, bool shell, std::integer_sequence<int, Ls...>) {
   constexpr int N0 = Dims<D>::N0;
   const float gm1 = a.gammaf - 1.0f;
   auto load = [&](int ox, int oy, int oz, float& rho, float& p) {
@@ -58,8 +61,23 @@ __device__ __forceinline__ void features(const GridArgs& a, const TU* __restrict
   };
   ((load(Off2<D, Ls>::x, Off2<D, Ls>::y, Off2<D, Ls>::z, f[Ls], f[N0 + Ls])), ...);
   constexpr int C = Geo<D, 2>::center();
-  normalise_block<N0, C>(f);
-  normalise_block<N0, C>(f + N0);
+  const float rc = f[C], pc = f[N0 + C];
+  const float dr = normalise_block<N0, C>(f);
+  const float dp = normalise_block<N0, C>(f + N0);
+  if (D == 3) {
+    float mr = 0.0f, mp = 0.0f;
+    if (shell) {
+#pragma unroll 6
+      for (int l = 0; l < 90; ++l) {
+        float r, p;
+        load(c_shell.off[l][0], c_shell.off[l][1], c_shell.off[l][2], r, p);
+        mr = fmaxf(mr, fabsf(r - rc));
+        mp = fmaxf(mp, fabsf(p - pc));
+      }
+    }
+    f[2 * N0] = shell_feature(mr, dr);
+    f[2 * N0 + 1] = shell_feature(mp, dp);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -67,14 +85,14 @@ __device__ __forceinline__ void features(const GridArgs& a, const TU* __restrict
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(256) features_kernel(GridArgs a, const double* __restrict__ U,
-                                                       float* __restrict__ X) {
+                                                       float* __restrict__ X, bool shell) {
   constexpr int NIN = Dims<D>::NIN;
   const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
   const long long c = blockIdx.x * 256LL + threadIdx.x;
   if (c >= ncell) return;
   const int x = (int)(c % a.n[0]), y = (int)((c / a.n[0]) % a.n[1]), z = (int)(c / ((long long)a.n[0] * a.n[1]));
   float f[NIN];
-  features<D>(a, U, ncell, x, y, z, f, std::make_integer_sequence<int, Dims<D>::N0>{});
+  features<D>(a, U, ncell, x, y, z, f, shell, std::make_integer_sequence<int, Dims<D>::N0>{});
 #pragma unroll
   for (int i = 0; i < NIN; ++i) X[c * NIN + i] = f[i];
 }
@@ -126,7 +144,8 @@ __global__ void __launch_bounds__(32 * kWarps) forward_kernel(const Pack<D>* __r
 template <int D, typename TU>
 __global__ void __launch_bounds__(32 * kWarps) mask_kernel(GridArgs a, const Pack<D>* __restrict__ pack,
                                                            const TU* __restrict__ U,
-                                                           unsigned char* __restrict__ mask, float zthresh) {
+                                                           unsigned char* __restrict__ mask, float zthresh,
+                                                           bool shell) {
   constexpr int NIN = Dims<D>::NIN, KIN = Dims<D>::KIN, LDX = Dims<D>::LDX;
   __shared__ Pack<D> P;
   __shared__ __align__(16) __nv_bfloat16 xs_all[kWarps][32 * LDX];
@@ -142,7 +161,7 @@ __global__ void __launch_bounds__(32 * kWarps) mask_kernel(GridArgs a, const Pac
     if (c < ncell) {
       const int x = (int)(c % a.n[0]), y = (int)((c / a.n[0]) % a.n[1]);
       const int z = (int)(c / ((long long)a.n[0] * a.n[1]));
-      features<D>(a, U, ncell, x, y, z, f, std::make_integer_sequence<int, Dims<D>::N0>{});
+      features<D>(a, U, ncell, x, y, z, f, shell, std::make_integer_sequence<int, Dims<D>::N0>{});
     } else {
 #pragma unroll
       for (int i = 0; i < NIN; ++i) f[i] = 0.0f;
@@ -368,10 +387,13 @@ static cudaError_t gate_mask_d(kfvm_ctx* ctx, const double* U, const float* shad
   const float th = (float)ctx->gate_threshold;
   const float zth = logf(th / (1.0f - th));
   const Pack<D>* P = (const Pack<D>*)ctx->d_gate_pack;
+  const bool shell = D == 3 && ctx->R >= 3;
   if (shadow)
-    mask_kernel<D, float><<<grid_for(ctx->ncell, kWarps), 32 * kWarps, 0, st>>>(a, P, shadow, ctx->d_gate_mask, zth);
+    mask_kernel<D, float><<<grid_for(ctx->ncell, kWarps), 32 * kWarps, 0, st>>>(a, P, shadow, ctx->d_gate_mask, zth,
+                                                                                 shell);
   else
-    mask_kernel<D, double><<<grid_for(ctx->ncell, kWarps), 32 * kWarps, 0, st>>>(a, P, U, ctx->d_gate_mask, zth);
+    mask_kernel<D, double><<<grid_for(ctx->ncell, kWarps), 32 * kWarps, 0, st>>>(a, P, U, ctx->d_gate_mask, zth,
+                                                                                  shell);
   ctx->launches += 1;
   return cudaGetLastError();
 }
@@ -384,13 +406,11 @@ cudaError_t launch_gate_mask(kfvm_ctx* ctx, const double* U, const float* shadow
 template <int D>
 static cudaError_t gate_features_d(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, cudaStream_t st) {
   const GridArgs a = make_grid_args(ctx);
-  features_kernel<D><<<(unsigned)((ctx->ncell + 255) / 256), 256, 0, st>>>(a, U, X);
+  features_kernel<D><<<(unsigned)((ctx->ncell + 255) / 256), 256, 0, st>>>(a, U, X, D == 3 && ctx->R >= 3);
   ctx->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_shadow(ctx, U, ctx->d_shadow, st);
-  if (e != cudaSuccess) return e;
-  return launch_labels(ctx, ctx->d_shadow, y, (float)(1.0 - tau), st);
+  return launch_labels(ctx, U, y, (float)(1.0 - tau), st);
 }
 
 cudaError_t launch_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, cudaStream_t st) {

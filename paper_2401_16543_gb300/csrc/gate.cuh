@@ -19,7 +19,8 @@ constexpr int kTrainWarps = 2;  // warps per CTA in the training kernel (shared-
 template <int D>
 struct Dims {
   static constexpr int N0 = Geo<D, 2>::N0;       // radius-2 stencil
-  static constexpr int NIN = 2 * N0;             // rho and p
+  static constexpr int NSH = (D == 3) ? 2 : 0;   // 3D: radius-3 shell inputs of rho and p
+  static constexpr int NIN = 2 * N0 + NSH;       // rho and p blocks (+ shell)
   static constexpr int KIN = (NIN + 15) / 16 * 16;
   static constexpr int LDX = KIN + 8;            // padded smem row (bank-conflict free fragment loads)
   // float32 master parameter offsets
@@ -133,17 +134,50 @@ __device__ __forceinline__ void load_pack(const Pack<D>* __restrict__ src, Pack<
 }
 
 // Normalise a feature block in place: deviations from the central value divided by
-// max(max |deviation|, 1e-6 |central value|) (+1e-30).
+// d = max(max |deviation|, 1e-5 |central value|) (+1e-30); returns d.  The floor keeps the
+// rounding of a float32 pressure (~1e-7 of E) below 0.05 in a block that is flat.
 template <int N0, int C>
-__device__ __forceinline__ void normalise_block(float* v) {
+__device__ __forceinline__ float normalise_block(float* v) {
   const float vc = v[C];
   float mx = 0.0f;
 #pragma unroll
   for (int l = 0; l < N0; ++l) mx = fmaxf(mx, fabsf(v[l] - vc));
-  const float inv = __frcp_rn(fmaxf(mx, 1e-6f * fabsf(vc) + 1e-30f));
+  const float d = fmaxf(mx, 1e-5f * fabsf(vc) + 1e-30f);
+  const float inv = __frcp_rn(d);
 #pragma unroll
   for (int l = 0; l < N0; ++l) v[l] = (v[l] - vc) * inv;
+  return d;
 }
+
+// 3D shell 4 < |o|^2 <= 9 (the radius-3 stencil minus the radius-2 one), z-outer, x fastest
+struct ShellTable {
+  int n;
+  int off[90][3];
+};
+constexpr ShellTable make_shell() {
+  ShellTable t{};
+  t.n = 0;
+  for (int k = -3; k <= 3; ++k)
+    for (int j = -3; j <= 3; ++j)
+      for (int i = -3; i <= 3; ++i) {
+        const int r2 = i * i + j * j + k * k;
+        if (r2 > 4 && r2 <= 9) {
+          t.off[t.n][0] = i;
+          t.off[t.n][1] = j;
+          t.off[t.n][2] = k;
+          ++t.n;
+        }
+      }
+  return t;
+}
+static_assert(make_shell().n == 90, "the radius-3 shell has 90 cells");
+template <int L>
+struct Shell {
+  static constexpr int x = make_shell().off[L][0], y = make_shell().off[L][1], z = make_shell().off[L][2];
+};
+
+// shell input of one block: m / (m + d), m = max |v_shell - v_c|, d = the block's normaliser
+__device__ __forceinline__ float shell_feature(float m, float d) { return m * __frcp_rn(m + d); }
 
 }  // namespace gate
 }  // namespace kfvm

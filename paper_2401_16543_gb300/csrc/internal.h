@@ -118,7 +118,7 @@ cudaError_t launch_flux_update(kfvm_ctx* ctx, int stage, const void* faces, cons
 // shadow != nullptr: features from the float32 shadow (mixed path), else from U
 cudaError_t launch_gate_mask(kfvm_ctx* ctx, const double* U, const float* shadow, cudaStream_t st);
 // WENO-AO training labels of the gate (float32 shadow input).
-cudaError_t launch_labels(kfvm_ctx* ctx, const float* shadow, float* y, float thresh, cudaStream_t st);
+cudaError_t launch_labels(kfvm_ctx* ctx, const double* U, float* y, float thresh, cudaStream_t st);
 cudaError_t launch_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, cudaStream_t st);
 cudaError_t launch_gate_forward(kfvm_ctx* ctx, const float* X, float* prob, size_t n, cudaStream_t st);
 cudaError_t launch_gate_train(kfvm_ctx* ctx, const float* X, const float* y, size_t n, float lr, float* loss,

@@ -8,16 +8,16 @@ cudaError_t launch_recon32_23(kfvm_ctx*, const double*, const float*, float*, cu
 cudaError_t launch_recon32_32(kfvm_ctx*, const double*, const float*, float*, cudaStream_t, int, int);
 cudaError_t launch_recon32_33(kfvm_ctx*, const double*, const float*, float*, cudaStream_t, int, int);
 
-cudaError_t launch_labels_22(kfvm_ctx*, const float*, float*, float, cudaStream_t);
-cudaError_t launch_labels_23(kfvm_ctx*, const float*, float*, float, cudaStream_t);
-cudaError_t launch_labels_32(kfvm_ctx*, const float*, float*, float, cudaStream_t);
-cudaError_t launch_labels_33(kfvm_ctx*, const float*, float*, float, cudaStream_t);
+cudaError_t launch_labels_22(kfvm_ctx*, const double*, float*, float, cudaStream_t);
+cudaError_t launch_labels_23(kfvm_ctx*, const double*, float*, float, cudaStream_t);
+cudaError_t launch_labels_32(kfvm_ctx*, const double*, float*, float, cudaStream_t);
+cudaError_t launch_labels_33(kfvm_ctx*, const double*, float*, float, cudaStream_t);
 
-cudaError_t launch_labels(kfvm_ctx* ctx, const float* shadow, float* y, float thresh, cudaStream_t st) {
-  if (ctx->dims == 2 && ctx->R == 2) return launch_labels_22(ctx, shadow, y, thresh, st);
-  if (ctx->dims == 2 && ctx->R == 3) return launch_labels_23(ctx, shadow, y, thresh, st);
-  if (ctx->dims == 3 && ctx->R == 2) return launch_labels_32(ctx, shadow, y, thresh, st);
-  return launch_labels_33(ctx, shadow, y, thresh, st);
+cudaError_t launch_labels(kfvm_ctx* ctx, const double* U, float* y, float thresh, cudaStream_t st) {
+  if (ctx->dims == 2 && ctx->R == 2) return launch_labels_22(ctx, U, y, thresh, st);
+  if (ctx->dims == 2 && ctx->R == 3) return launch_labels_23(ctx, U, y, thresh, st);
+  if (ctx->dims == 3 && ctx->R == 2) return launch_labels_32(ctx, U, y, thresh, st);
+  return launch_labels_33(ctx, U, y, thresh, st);
 }
 
 cudaError_t launch_recon32(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st,

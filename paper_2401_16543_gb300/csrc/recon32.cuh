@@ -80,14 +80,34 @@ struct Dlt2 {
                            T32<D, R>::SX * (Geo<D, 2>::tab.off[L][1] + T32<D, R>::SY * Geo<D, 2>::tab.off[L][2]);
 };
 
+// offsets of the 3D radius-3 shell (the gate's shell inputs) in the tile of radius R >= 3
+template <int D, int R, int L>
+struct DltS {
+  static constexpr int v = gate::Shell<L>::x + T32<D, R>::SX * (gate::Shell<L>::y + T32<D, R>::SY * gate::Shell<L>::z);
+};
+
+template <int D, int R, int... Ss>
+__device__ __forceinline__ void shell_max(const float* __restrict__ sm, const float* __restrict__ sp, int c, float rc,
+                                          float pc, float& mr, float& mp, std::integer_sequence<int, Ss...>) {
+  ((mr = fmaxf(mr, fabsf(sm[c + DltS<D, R, Ss>::v] - rc)), mp = fmaxf(mp, fabsf(sp[c + DltS<D, R, Ss>::v] - pc))),
+   ...);
+}
+
 template <int D, int R, int... Ls>
 __device__ __forceinline__ void gate_features_tile(const float* __restrict__ sm, const float* __restrict__ sp, int c,
                                                    float* f, std::integer_sequence<int, Ls...>) {
   constexpr int N0 = Geo<D, 2>::N0;
   ((f[Ls] = sm[c + Dlt2<D, R, Ls>::v]), ...);
   ((f[N0 + Ls] = sp[c + Dlt2<D, R, Ls>::v]), ...);
-  gate::normalise_block<N0, Geo<D, 2>::center()>(f);
-  gate::normalise_block<N0, Geo<D, 2>::center()>(f + N0);
+  const float rc = sm[c], pc = sp[c];
+  const float dr = gate::normalise_block<N0, Geo<D, 2>::center()>(f);
+  const float dp = gate::normalise_block<N0, Geo<D, 2>::center()>(f + N0);
+  if constexpr (D == 3) {
+    float mr = 0.0f, mp = 0.0f;
+    if constexpr (R >= 3) shell_max<D, R>(sm, sp, c, rc, pc, mr, mp, std::make_integer_sequence<int, 90>{});
+    f[2 * N0] = gate::shell_feature(mr, dr);
+    f[2 * N0 + 1] = gate::shell_feature(mp, dp);
+  }
 }
 
 // dynamic shared memory of recon32_kernel (floats), and where the gate's pieces sit
@@ -479,103 +499,147 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
 // by the weights (omega_0/gamma_0 >= thresh = 1 - tau) or varies over the
 // stencil by less than 1e-6 of its scale (rho~ for density, p~ for pressure,
 // the sound speed for velocities), where WENO-AO and the linear
-// reconstruction differ by less than that; else 0.
+// reconstruction differ by less than that; else 0.  The lin-prim deltas are
+// formed in float64 from the float64 state (a float32 shadow would leave
+// rounding noise of ~1e-7 of E in components that are constant, and the
+// weights of noise are random); the indicators then run in float32 as in the
+// reconstruction.
 template <int D, int R>
-__global__ void __launch_bounds__(T32<D, R>::THREADS) label_kernel(GridArgs a, const float* __restrict__ S,
-                                                                   float* __restrict__ y, float thresh,
-                                                                   const __grid_constant__ W32<D, R> W) {
-  using G = Geo<D, R>;
+__device__ __forceinline__ float delta64(const double* __restrict__ sm, int o, int v, const double* uc,
+                                         const double* ut, double kin, double irt, double gm1) {
+  constexpr int SN = T32<D, R>::SN;
+  const double dr = sm[o] - uc[0];
+  if (v == 0) return (float)dr;
+  if (v <= D) return (float)(fma(-ut[v - 1], dr, sm[v * SN + o] - uc[v]) * irt);
+  double t = fma(kin, dr, sm[(D + 1) * SN + o] - uc[D + 1]);
+#pragma unroll
+  for (int k = 0; k < D; ++k) t = fma(-ut[k], sm[(1 + k) * SN + o] - uc[1 + k], t);
+  return (float)(gm1 * t);
+}
+
+// float64 tile of the state (+ halo R); every label kernel stages it the same way
+template <int D, int R>
+__device__ __forceinline__ void stage64(const GridArgs& a, const double* __restrict__ U, double* sm, int x0, int y0,
+                                        int z0) {
   using T = T32<D, R>;
-  constexpr int NV = G::NV, SN = T::SN, NQ = G::NQ, N0 = G::N0;
-  extern __shared__ float smem32[];
-  float* sm = smem32;
+  constexpr int NV = D + 2;
   const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
-  const float gm1 = a.gammaf - 1.0f;
-  const int tiles_x = (a.n[0] + T::TX - 1) / T::TX, tiles_y = (a.n[1] + T::TY - 1) / T::TY;
-  int b = blockIdx.x;
-  const int bx = b % tiles_x;
-  b /= tiles_x;
-  const int by = b % tiles_y;
-  const int bz = b / tiles_y;
-  const int x0 = bx * T::TX - T::H, y0 = by * T::TY - T::H, z0 = (D == 3) ? bz * T::TZ - T::H : 0;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < SN; i += T::THREADS) {
+  for (int i = threadIdx.x; i < T::SN; i += T::THREADS) {
     const int sx = i % T::SX, sy = (i / T::SX) % T::SY, sz = i / (T::SX * T::SY);
     const int gx = map_index(x0 + sx, a.n[0], a.bc[0][0], a.bc[0][1]);
     const int gy = map_index(y0 + sy, a.n[1], a.bc[1][0], a.bc[1][1]);
     const int gz = (D == 3) ? map_index(z0 + sz, a.n[2], a.bc[2][0], a.bc[2][1]) : 0;
     const long long gc = ((long long)gz * a.n[1] + gy) * a.n[0] + gx;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sm[v * SN + i] = S[v * ncell + gc];
+    for (int v = 0; v < NV; ++v) sm[v * T::SN + i] = U[v * ncell + gc];
   }
+}
+
+// reference quantities of a cell from the float64 tile: state, velocity, kinetic energy per
+// mass, 1/rho, and the amplitude scales (rho, sound speed, p)
+template <int D, int R>
+struct Ref64 {
+  double uc[D + 2], ut[3] = {0.0, 0.0, 0.0}, kin = 0.0, irt, gm1, scale[3];
+  __device__ __forceinline__ Ref64(const double* __restrict__ sm, int c, double gamma) : gm1(gamma - 1.0) {
+    constexpr int SN = T32<D, R>::SN;
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) uc[v] = sm[v * SN + c];
+    irt = 1.0 / uc[0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      ut[k] = uc[1 + k] * irt;
+      kin = fma(ut[k], ut[k], kin);
+    }
+    kin *= 0.5;
+    const double p = gm1 * (uc[D + 1] - uc[0] * kin);
+    scale[0] = uc[0];
+    scale[1] = sqrt(fmax(gamma * p * irt, 0.0));
+    scale[2] = p;
+  }
+  __device__ __forceinline__ double scale_of(int v) const { return v == 0 ? scale[0] : (v == D + 1 ? scale[2] : scale[1]); }
+  __device__ __forceinline__ float delta(const double* __restrict__ sm, int o, int v) const {
+    return delta64<D, R>(sm, o, v, uc, ut, kin, irt, gm1);
+  }
+};
+
+// lin-prim deltas of variable v over S0 (float64, rounded to float32); returns max |delta|
+template <int D, int R, int... Ls>
+__device__ __forceinline__ float load_deltas64(const Ref64<D, R>& r, const double* __restrict__ sm, int c, int v,
+                                               float (&g)[Geo<D, R>::N0], std::integer_sequence<int, Ls...>) {
+  float amp = 0.0f;
+  ((g[Ls] = r.delta(sm, c + Dlt<D, R, Ls>::v, v), amp = fmaxf(amp, fabsf(g[Ls]))), ...);
+  return amp;
+}
+
+// omega_0 / gamma_0 from the indicators (Eq. 24, scaled form)
+template <int D, int NQ>
+__device__ __forceinline__ float omega0_ratio(const float (&beta)[NQ], float epsf) {
+  float bmax = 0.0f;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) bmax = fmaxf(bmax, beta[q]);
+  if (!(bmax > 0.0f)) return 1.0f;
+  const float ib = __frcp_rn(bmax);
+  const float e = fmaxf(epsf * ib * ib, 1e-30f);
+  float om0 = 0.0f, sum = 0.0f;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const float bq = beta[q] * ib;
+    const float o = __fdividef((float)linear_weight<D>(q), fmaf(bq, bq, e));
+    if (q == 0) om0 = o;
+    sum += o;
+  }
+  return om0 / (sum * (float)linear_weight<D>(0));
+}
+
+template <int D, int R>
+__global__ void __launch_bounds__(T32<D, R>::THREADS) label_kernel(GridArgs a, const double* __restrict__ U,
+                                                                   float* __restrict__ y, float thresh,
+                                                                   const __grid_constant__ W32<D, R> W) {
+  using G = Geo<D, R>;
+  using T = T32<D, R>;
+  constexpr int NV = G::NV, NQ = G::NQ, N0 = G::N0;
+  extern __shared__ double smem64l[];
+  const int tiles_x = (a.n[0] + T::TX - 1) / T::TX, tiles_y = (a.n[1] + T::TY - 1) / T::TY;
+  int b = blockIdx.x;
+  const int bx = b % tiles_x;
+  b /= tiles_x;
+  const int by = b % tiles_y;
+  const int bz = b / tiles_y;
+  stage64<D, R>(a, U, smem64l, bx * T::TX - T::H, by * T::TY - T::H, (D == 3) ? bz * T::TZ - T::H : 0);
   __syncthreads();
+  const int tid = threadIdx.x;
   const int lx = tid % T::TX, ly = (tid / T::TX) % T::TY, lz = tid / (T::TX * T::TY);
   const int x = bx * T::TX + lx, yy = by * T::TY + ly, z = (D == 3) ? bz * T::TZ + lz : 0;
   if (x >= a.n[0] || yy >= a.n[1] || z >= a.n[2]) return;
   const long long cell = ((long long)z * a.n[1] + yy) * a.n[0] + x;
   const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (D == 3 ? lz + T::H : 0));
-  float uc[NV], ut[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int v = 0; v < NV; ++v) uc[v] = sm[v * SN + c];
-  const float irt = __frcp_rn(uc[0]);
-  float kin = 0.0f;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    ut[k] = uc[1 + k] * irt;
-    kin = fmaf(ut[k], ut[k], kin);
-  }
-  kin *= 0.5f;
+  const Ref64<D, R> r(smem64l, c, a.gamma);
   float worst = 1.0f;
-  float g[N0];
-  // component scales of the amplitude clause
-  float m2c = 0.0f;
-#pragma unroll
-  for (int k = 0; k < D; ++k) m2c = fmaf(uc[1 + k], uc[1 + k], m2c);
-  const float pc = gm1 * fmaf(-0.5f * m2c, irt, uc[D + 1]);
-  const float cs = sqrtf(fmaxf(a.gammaf * pc * irt, 0.0f));
 #pragma unroll 1
   for (int v = 0; v < NV; ++v) {
-    gather_row<D, R>(sm, c, v, g, uc, ut, kin, irt, gm1, std::make_integer_sequence<int, N0>{});
-    float amp = 0.0f;
-#pragma unroll
-    for (int l = 0; l < N0; ++l) amp = fmaxf(amp, fabsf(g[l]));
-    const float scale = (v == 0) ? uc[0] : (v == NV - 1 ? pc : cs);
-    if (amp <= 1e-6f * scale) continue;  // negligible variation: smooth whatever the weights say
+    float g[N0];
+    const float amp = load_deltas64<D, R>(r, smem64l, c, v, g, std::make_integer_sequence<int, N0>{});
+    if ((double)amp <= 1e-6 * r.scale_of(v)) continue;  // negligible variation: smooth whatever the weights
     float beta[NQ];
     all_betas<D, R>(W, g, beta, std::make_integer_sequence<int, NQ>{});
-    float bmax = 0.0f;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) bmax = fmaxf(bmax, beta[q]);
-    float ratio = 1.0f;
-    if (bmax > 0.0f) {
-      const float ib = __frcp_rn(bmax);
-      const float e = fmaxf(a.epsf * ib * ib, 1e-30f);
-      float om0 = 0.0f, sum = 0.0f;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const float bq = beta[q] * ib;
-        const float o = __fdividef((float)linear_weight<D>(q), fmaf(bq, bq, e));
-        if (q == 0) om0 = o;
-        sum += o;
-      }
-      ratio = om0 / (sum * (float)linear_weight<D>(0));
-    }
-    worst = fminf(worst, ratio);
+    worst = fminf(worst, omega0_ratio<D, NQ>(beta, a.epsf));
   }
   y[cell] = worst >= thresh ? 1.0f : 0.0f;
 }
 
 template <int D, int R>
-cudaError_t launch_labels(kfvm_ctx* ctx, const float* shadow, float* y, float thresh, cudaStream_t st) {
+cudaError_t launch_labels(kfvm_ctx* ctx, const double* U, float* y, float thresh, cudaStream_t st) {
   using T = T32<D, R>;
   using G = Geo<D, R>;
   const GridArgs a = make_grid_args(ctx);
   const int tiles = ((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
                     ((D == 3) ? (ctx->n[2] + T::TZ - 1) / T::TZ : 1);
-  const size_t smem = sizeof(float) * G::NV * T::SN;
+  const size_t smem = sizeof(double) * G::NV * T::SN;
+  cudaError_t e = cudaFuncSetAttribute(label_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   std::unique_ptr<W32<D, R>> wp(new W32<D, R>);
   for (int i = 0; i < G::WCOUNT; ++i) wp->w[i] = (float)ctx->w_host[i];
-  label_kernel<D, R><<<tiles, T::THREADS, smem, st>>>(a, shadow, y, thresh, *wp);
+  label_kernel<D, R><<<tiles, T::THREADS, smem, st>>>(a, U, y, thresh, *wp);
   ctx->launches += 1;
   return cudaGetLastError();
 }

@@ -7,7 +7,7 @@ cudaError_t launch_recon32_22(kfvm_ctx* ctx, const double* U, const float* shado
                                 cudaStream_t st, int zf_first, int zf_count) {
   return r32::launch<2, 2>(ctx, U, shadow, faces, st, zf_first, zf_count);
 }
-cudaError_t launch_labels_22(kfvm_ctx* ctx, const float* shadow, float* y, float thresh, cudaStream_t st) {
-  return r32::launch_labels<2, 2>(ctx, shadow, y, thresh, st);
+cudaError_t launch_labels_22(kfvm_ctx* ctx, const double* U, float* y, float thresh, cudaStream_t st) {
+  return r32::launch_labels<2, 2>(ctx, U, y, thresh, st);
 }
 }  // namespace kfvm

@@ -98,8 +98,8 @@ struct Ref {
 };
 
 // smoothness indicators beta_q (Eq. 22) of every stencil for one (cell, variable)
-__device__ __forceinline__ void betas(const float* __restrict__ sm, int cc, const Ref& r,
-                                      const float4* __restrict__ Wt, float (&beta)[NQ]) {
+template <class Delta>
+__device__ __forceinline__ void betas(int cc, Delta delta, const float4* __restrict__ Wt, float (&beta)[NQ]) {
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     float d[MP];
@@ -107,7 +107,7 @@ __device__ __forceinline__ void betas(const float* __restrict__ sm, int cc, cons
     for (int m = 0; m < MP; ++m) d[m] = 0.0f;
 #pragma unroll 2
     for (int k = c_pairs.start[q]; k < c_pairs.start[q + 1]; ++k) {
-      const float g = r.delta(sm, cc + c_pairs.off[k]);
+      const float g = delta(cc + c_pairs.off[k]);
       const float4* wr = Wt + k * ROW4 + FP / 4;
 #pragma unroll
       for (int m4 = 0; m4 < MP / 4; ++m4) {
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(TH, 3) recon33_kernel(GridArgs a, int mode, co
     for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
     if (!linear) {
       float beta[NQ];
-      betas(sm, cc, r, Wt, beta);
+      betas(cc, [&](int o) { return r.delta(sm, o); }, Wt, beta);
       // nonlinear weights in the scaled form (Eq. 24) and the WENO-AO coefficients (Eq. 25)
       float bmax = 0.0f;
 #pragma unroll
@@ -308,21 +308,18 @@ __global__ void __launch_bounds__(TH, 3) recon33_kernel(GridArgs a, int mode, co
                           [&](int s, int v) { return *slot(faces, ncell_f, fcell, s, v); });
 }
 
-// Training labels of the learned gate for d = 3, R = 3: the same rule as r32::label_kernel
-// (every linearized primitive component smooth by its own WENO-AO weights, omega_0/gamma_0 >=
-// thresh, or varying over S0 by less than 1e-6 of its scale).
-__global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const float* __restrict__ S, float* __restrict__ y,
+// Training labels of the learned gate for d = 3, R = 3: the rule of r32::label_kernel
+// (float64 lin-prim deltas, float32 indicators), with the rolled contraction above.
+__global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* __restrict__ U, float* __restrict__ y,
                                                      float thresh, const float4* __restrict__ Wt) {
-  extern __shared__ float smem33[];
-  float* sm = smem33;
-  float* sp = sm + NV * SN;
+  extern __shared__ double smem33l[];
   const int tiles_x = (a.n[0] + T::TX - 1) / T::TX, tiles_y = (a.n[1] + T::TY - 1) / T::TY;
   int b = blockIdx.x;
   const int bx = b % tiles_x;
   b /= tiles_x;
   const int by = b % tiles_y;
   const int bz = b / tiles_y;
-  stage_tile(a, S, sm, sp, bx * T::TX - T::H, by * T::TY - T::H, bz * T::TZ - T::H);
+  r32::stage64<3, 3>(a, U, smem33l, bx * T::TX - T::H, by * T::TY - T::H, bz * T::TZ - T::H);
   __syncthreads();
   const int tid = threadIdx.x;
   const int lx = tid % T::TX, ly = (tid / T::TX) % T::TY, lz = tid / (T::TX * T::TY);
@@ -330,38 +327,18 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const float* __
   if (x >= a.n[0] || yy >= a.n[1] || z >= a.n[2]) return;
   const long long cell = ((long long)z * a.n[1] + yy) * a.n[0] + x;
   const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (lz + T::H));
-  const float gm1 = a.gammaf - 1.0f;
+  const r32::Ref64<3, 3> r(smem33l, c, a.gamma);
   float worst = 1.0f;
 #pragma unroll 1
   for (int v = 0; v < NV; ++v) {
-    const Ref r(sm, c, v, gm1);
+    auto delta = [&](int o) { return r.delta(smem33l, o, v); };
     float amp = 0.0f;
 #pragma unroll 4
-    for (int k = 0; k < c_pairs.start[1]; ++k) amp = fmaxf(amp, fabsf(r.delta(sm, c + c_pairs.off[k])));
-    const float pc = sp[c];
-    const float cs = sqrtf(fmaxf(a.gammaf * pc * r.irt, 0.0f));
-    const float scale = (v == 0) ? r.uc[0] : (v == NV - 1 ? pc : cs);
-    if (amp <= 1e-6f * scale) continue;
+    for (int k = 0; k < c_pairs.start[1]; ++k) amp = fmaxf(amp, fabsf(delta(c + c_pairs.off[k])));
+    if ((double)amp <= 1e-6 * r.scale_of(v)) continue;
     float beta[NQ];
-    betas(sm, c, r, Wt, beta);
-    float bmax = 0.0f;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) bmax = fmaxf(bmax, beta[q]);
-    float ratio = 1.0f;
-    if (bmax > 0.0f) {
-      const float ib = __frcp_rn(bmax);
-      const float e = fmaxf(a.epsf * ib * ib, 1e-30f);
-      float om0 = 0.0f, sum = 0.0f;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const float bq = beta[q] * ib;
-        const float o = __fdividef((float)linear_weight<3>(q), fmaf(bq, bq, e));
-        if (q == 0) om0 = o;
-        sum += o;
-      }
-      ratio = om0 / (sum * (float)linear_weight<3>(0));
-    }
-    worst = fminf(worst, ratio);
+    betas(c, delta, Wt, beta);
+    worst = fminf(worst, r32::omega0_ratio<3, NQ>(beta, a.epsf));
   }
   y[cell] = worst >= thresh ? 1.0f : 0.0f;
 }
@@ -413,13 +390,15 @@ cudaError_t launch_recon32_33(kfvm_ctx* ctx, const double* U, const float* shado
 }  // namespace kfvm
 
 namespace kfvm {
-cudaError_t launch_labels_33(kfvm_ctx* ctx, const float* shadow, float* y, float thresh, cudaStream_t st) {
+cudaError_t launch_labels_33(kfvm_ctx* ctx, const double* U, float* y, float thresh, cudaStream_t st) {
   using namespace r33;
   const GridArgs a = make_grid_args(ctx);
   const int tiles = ((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
                     ((ctx->n[2] + T::TZ - 1) / T::TZ);
-  label33_kernel<<<tiles, TH, sizeof(float) * Smem::base, st>>>(a, shadow, y, thresh,
-                                                                reinterpret_cast<const float4*>(ctx->d_w32));
+  const size_t smem = sizeof(double) * NV * SN;
+  cudaError_t e = cudaFuncSetAttribute(label33_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  label33_kernel<<<tiles, TH, smem, st>>>(a, U, y, thresh, reinterpret_cast<const float4*>(ctx->d_w32));
   ctx->launches += 1;
   return cudaGetLastError();
 }

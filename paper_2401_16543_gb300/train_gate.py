@@ -17,6 +17,12 @@ tensor cores, FP32 accumulation, Adam on FP32 masters; 20 epochs of batches of
 as float32 .npy in the packing of kfvm_gate_set_params.
 
     python -m paper_2401_16543_gb300.train_gate --out paper_2401_16543_gb300/gate_params_2d.npy
+
+3D (radius-3 labels; the radius-2 stencils of rho and p plus the two radius-3 shell
+inputs): pairs from a 48^3 smooth run and two 128^3 runs (generate_3d), written to
+gate_params_3d.npy:
+
+    python -m paper_2401_16543_gb300.train_gate --dims 3 --radius 3
 """
 from __future__ import annotations
 
@@ -31,7 +37,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(HERE))
 
-DEFAULT_OUT = os.path.join(HERE, "gate_params_2d.npy")
+DEFAULT_OUT = {2: os.path.join(HERE, "gate_params_2d.npy"), 3: os.path.join(HERE, "gate_params_3d.npy")}
 
 
 def init_params(n_in: int, seed: int) -> np.ndarray:
@@ -74,6 +80,43 @@ def generate(tau: float, voronoi_n: int = 1024, voronoi_steps: int = 200, every:
     return torch.cat(Xs), torch.cat(ys)
 
 
+def generate_3d(tau: float, n: int = 128, steps: int = 30, every: int = 6, R: int = 3, device="cuda"):
+    """Pooled (X, y) from 3D runs at radius R, FP32 WENO-AO everywhere, CFL 0.4:
+    the smooth translation on 48^3 cells (periodic, every step to t = 0.05), the
+    half-sine / half-Voronoi state (16 regions in x >= 1/2, seed 3, periodic) and the
+    mixed state (16 regions, each smooth or constant, seed 5, outflow) on n^3 cells,
+    features and labels of every `every`-th of `steps` SSP-RK3 steps."""
+    import torch
+
+    import workloads
+    from paper_2401_16543_gb300 import KFVM
+    Xs, ys = [], []
+    g = KFVM([48, 48, 48], dims=3, radius=R, bc="periodic")
+    g.set_option("precision", 32)
+    U = workloads.sine_3d(48, R=R, device=device).contiguous()
+    t = 0.0
+    while t < 0.05:
+        X, y = g.gate_features(U, tau)
+        Xs.append(X)
+        ys.append(y)
+        t += g.step(U, 0.4, 0.05 - t)
+    del U, g
+    for make, bc in ((lambda: workloads.half_sine_voronoi_3d(n, k=16, seed=3, R=R, device=device), "periodic"),
+                     (lambda: workloads.mixed_voronoi(3, n, 16, seed=5, R=R, device=device), "outflow")):
+        g = KFVM([n, n, n], dims=3, radius=R, bc=bc)
+        g.set_option("precision", 32)
+        U = make().contiguous()
+        for k in range(steps + 1):
+            if k % every == 0:
+                X, y = g.gate_features(U, tau)
+                Xs.append(X)
+                ys.append(y)
+            if k < steps:
+                g.step(U, 0.4)
+        del U, g
+    return torch.cat(Xs), torch.cat(ys)
+
+
 def train(X, y, pairs: int, epochs: int, batch: int, lr: float, seed: int = 41, init_seed: int = 0,
           log=print):
     """Train on `pairs` samples drawn with `seed`; returns (params, held-out metrics, loss history)."""
@@ -92,7 +135,8 @@ def train(X, y, pairs: int, epochs: int, batch: int, lr: float, seed: int = 41, 
     tr, ho = idx[:-n_hold], idx[-n_hold:]
     Xtr, ytr = X[tr].contiguous(), y[tr].contiguous()
     Xho, yho = X[ho].contiguous(), y[ho].contiguous()
-    g = KFVM([8, 8], dims=2, radius=2)
+    dims = 2 if X.shape[1] == 26 else 3
+    g = KFVM([8] * dims, dims=dims, radius=2)
     g.gate_set_params(init_params(X.shape[1], init_seed))
     loss = torch.zeros(1, dtype=torch.float32, device=X.device)
     hist = []
@@ -125,7 +169,9 @@ def train(X, y, pairs: int, epochs: int, batch: int, lr: float, seed: int = 41, 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--out", default=DEFAULT_OUT)
+    ap.add_argument("--dims", type=int, default=2, choices=(2, 3))
+    ap.add_argument("--radius", type=int, default=3, help="3D only: radius of the labelling WENO-AO")
+    ap.add_argument("--out", default=None)
     ap.add_argument("--pairs", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batch", type=int, default=16384)
@@ -133,13 +179,13 @@ def main():
     ap.add_argument("--tau", type=float, default=0.5)
     args = ap.parse_args()
     t0 = time.time()
-    X, y = generate(args.tau)
+    X, y = generate(args.tau) if args.dims == 2 else generate_3d(args.tau, R=args.radius)
     print(f"generated {X.shape[0]} pairs in {time.time() - t0:.1f} s; smooth label fraction {y.mean().item():.3f}")
     t1 = time.time()
     params, metrics, hist = train(X, y, args.pairs, args.epochs, args.batch, args.lr)
     metrics["train_seconds"] = time.time() - t1
     metrics["loss_history"] = hist
-    np.save(args.out, params.astype(np.float32))
+    np.save(args.out or DEFAULT_OUT[args.dims], params.astype(np.float32))
     print(json.dumps(metrics))
 
 

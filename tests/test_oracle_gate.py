@@ -81,8 +81,47 @@ def test_features_match_direct_stencil_loop():
             c = s0.index((0, 0, 0))
             for v in (rho, p):
                 d = v - v[c]
-                want.append(d / max(np.abs(d).max(), 1e-6 * abs(v[c]) + 1e-30))
+                want.append(d / max(np.abs(d).max(), 1e-5 * abs(v[c]) + 1e-30))
             assert np.allclose(f[j * n + i], np.concatenate(want), atol=1e-13)
+
+
+def test_3d_shell_features_see_a_jump_three_cells_away():
+    """A density jump at distance 3 from a cell is invisible to the radius-2 blocks (exactly zero)
+    but sets the radius-3 shell input of rho to ~1; constant data gives zero shell inputs; the
+    shell inputs are zero when the reconstruction radius is 2; a brute-force loop over the 90
+    shell offsets agrees."""
+    n = 10
+    C = workloads.constant_state(3, [n, n, n])
+    U = C.clone().numpy()
+    U[:, :, :, 6:] *= 2.0  # rho, m, E doubled for x >= 6: a jump in rho (and p), velocity unchanged
+    f = gate.features(U, 3, "outflow", R=3)
+    assert f.shape == (n ** 3, 68) and gate.n_in(3) == 68
+    assert len(gate.shell_offsets()) == 90
+    cell = (5 * n + 5) * n + 3  # x = 3: the jump is 3 cells away
+    assert np.abs(f[cell, :66]).max() == 0.0
+    assert f[cell, 66] > 0.99 and f[cell, 67] > 0.99
+    far = (5 * n + 5) * n + 1  # x = 1: 5 cells away
+    assert np.abs(f[far]).max() == 0.0
+    assert np.abs(gate.features(C.numpy(), 3, "outflow", R=3)).max() == 0.0
+    assert np.abs(gate.features(U, 3, "outflow", R=2)[:, 66:]).max() == 0.0
+    # brute force on a periodic smooth/constant mix
+    m = 7
+    V = workloads.mixed_voronoi(3, m, 3, seed=12).numpy()
+    fv = gate.features(V, 3, "periodic", R=3)
+    sh = gate.shell_offsets()
+    s0 = oracle.stencils.full_stencil(3, 2)
+    for k, j, i in [(0, 0, 0), (3, 5, 1), (6, 2, 4)]:
+        def at(o, v):
+            return V[v, (k + o[2]) % m, (j + o[1]) % m, (i + o[0]) % m]
+        for blk in range(2):
+            if blk == 0:
+                val = lambda o: at(o, 0)  # noqa: E731
+            else:
+                val = lambda o: 0.4 * (at(o, 4) - 0.5 * sum(at(o, 1 + q) ** 2 for q in range(3)) / at(o, 0))  # noqa: E731
+            vc = val((0, 0, 0))
+            d = max(max(abs(val(o) - vc) for o in s0), 1e-5 * abs(vc) + 1e-30)
+            ms = max(abs(val(o) - vc) for o in sh)
+            assert abs(fv[(k * m + j) * m + i, 66 + blk] - ms / (ms + d)) <= 1e-13
 
 
 def test_bf16_rounding():

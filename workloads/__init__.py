@@ -116,6 +116,22 @@ def sine_2d_exact_density(n: int, t: float) -> np.ndarray:
     return 1.0 + 0.2 * np.sin(2 * math.pi * (X + Y - 2 * t)) * damp
 
 
+def sine_3d(n: int, R: int = 3, device="cpu") -> torch.Tensor:
+    """The C3 smooth state on the periodic unit cube: rho = 1 + 0.2 sin(2 pi (x + y + z)), velocity 1, p = 1."""
+    h = 1.0 / n
+    return _cell_average(lambda c: _sine_prim(c, 3), 3, [n, n, n], [0.0] * 3, [h] * 3, R, device)
+
+
+def sine_3d_exact_density(n: int, t: float) -> np.ndarray:
+    """Exact cell averages of rho at time t for ``sine_3d`` ([z][y][x]): translation by (t, t, t),
+    cell average = point value times (sin(pi h)/(pi h))^3."""
+    h = 1.0 / n
+    xc = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+    damp = (math.sin(math.pi * h) / (math.pi * h)) ** 3
+    return 1.0 + 0.2 * np.sin(2 * math.pi * (X + Y + Z - 3 * t)) * damp
+
+
 def _draw_regions(rng: SplitMix64, k: int, dim: int, site_lo, site_hi, with_coin: bool):
     sites = np.array([[rng.uniform(site_lo[a], site_hi[a]) for a in range(dim)] for _ in range(k)])
     states = []
