@@ -1,10 +1,14 @@
 #!/usr/bin/env python
 """Throughput of the KFVM-WENO hot path on one GB300 (or N replicas under torchrun).
 
-Metric: cell-updates/s per RK stage (cells x RK stages / time) of SSP-RK3 steps of
-the 2D Euler workload on 1024 x 1024 cells: radius-2 KFVM-WENO-AO, HLLC, the
-positivity limiter, outflow boundaries, 64 seeded Voronoi regions with
-rho, p ~ U[0.1, 1] and u, v ~ U[-1, 1] (seed 2), CFL 0.4.
+Metric: cell-updates/s per RK stage (cells x RK stages / time) of SSP-RK3 steps.
+The default workload is the 2D Euler problem on 1024 x 1024 cells: radius-2
+KFVM-WENO-AO, HLLC, the positivity limiter, outflow boundaries, 64 seeded
+Voronoi regions with rho, p ~ U[0.1, 1] and u, v ~ U[-1, 1] (seed 2), CFL 0.4.
+``--workload`` selects the other synthetic workloads (3D 256^3 half smooth /
+half Voronoi at radius 2; 2D 2048^2 mixed smooth/constant regions; 3D 512^3
+mixed regions at radius 3, whose plain FP64 comparison runs on a slab of
+z-planes because that path takes seconds per stage).
 
 One printed JSON line (rank 0).  A "step" is one SSP-RK3 step: the CFL
 reduction and three RK stages (Riemann states, face fluxes, update), all in the
@@ -28,13 +32,61 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_GRID = 1024
-RADIUS = 2
 CFL = 0.4
 METRIC = "cell-updates/s per RK stage"
-WORKLOAD = ("2D Euler 1024x1024, radius-2 KFVM-WENO-AO (linearized primitive variables), HLLC + Batten, "
-            "positivity limiter, outflow, 64 seeded Voronoi regions (rho,p~U[0.1,1], u,v~U[-1,1], seed 2), "
-            "SSP-RK3 at CFL 0.4")
+GATE_THRESHOLD = 0.8
+
+
+class Workload:
+    def __init__(self, name, dims, R, n, bc, desc, make, gate=None, fp64_planes=None, cpu_crop=None):
+        self.name, self.dims, self.R, self.n, self.bc, self.desc = name, dims, R, n, bc, desc
+        self.make = make                  # device -> float64 state
+        self.gate = gate                  # trained gate parameters (.npy) or None
+        self.fp64_planes = fp64_planes    # 3D: time the plain FP64 path on this many z-planes
+        self.cpu_crop = cpu_crop          # edge of the cube / square the oracle times
+
+    @property
+    def ncell(self):
+        c = 1
+        for v in self.n:
+            c *= v
+        return c
+
+    def gate_path(self):
+        return os.path.join(ROOT, "paper_2401_16543_gb300", self.gate) if self.gate else None
+
+    def has_gate(self):
+        return self.gate is not None and os.path.exists(self.gate_path())
+
+
+def _workloads():
+    import workloads as wl
+    return {
+        "voronoi2d-1024": Workload(
+            "voronoi2d-1024", 2, 2, [1024, 1024], "outflow",
+            "2D Euler 1024x1024, radius-2 KFVM-WENO-AO (linearized primitive variables), HLLC + Batten, positivity "
+            "limiter, outflow, 64 seeded Voronoi regions (rho,p~U[0.1,1], u,v~U[-1,1], seed 2), SSP-RK3 at CFL 0.4",
+            lambda dev: wl.voronoi_2d(1024, k=64, seed=2, device=dev), gate="gate_params_2d.npy", cpu_crop=128),
+        "halfsine3d-256": Workload(
+            "halfsine3d-256", 3, 2, [256, 256, 256], "periodic",
+            "3D Euler 256^3 periodic, radius 2: x<1/2 smooth sine advection, x>=1/2 128 seeded Voronoi regions "
+            "(seed 3), FP32 mixed path vs plain FP64, SSP-RK3 at CFL 0.4",
+            lambda dev: wl.half_sine_voronoi_3d(256, k=128, seed=3, device=dev), gate=None, cpu_crop=24),
+        "mixed2d-2048": Workload(
+            "mixed2d-2048", 2, 2, [2048, 2048], "outflow",
+            "2D Euler 2048x2048, radius 2, learned gate: 256 seeded Voronoi regions (seed 4), each smooth sine or a "
+            "constant (coin 1/2), outflow, SSP-RK3 at CFL 0.4",
+            lambda dev: wl.mixed_voronoi(2, 2048, 256, seed=4, device=dev), gate="gate_params_2d.npy", cpu_crop=128),
+        "mixed3d-512-r3": Workload(
+            "mixed3d-512-r3", 3, 3, [512, 512, 512], "outflow",
+            "3D Euler 512^3, radius 3, learned gate + mixed precision: 512 seeded Voronoi regions (seed 5), each smooth "
+            "sine or a constant, outflow, SSP-RK3 at CFL 0.4; plain FP64 timed on 16 z-planes of the same state",
+            lambda dev: wl.mixed_voronoi(3, 512, 512, seed=5, R=3, device=dev), gate="gate_params_3d.npy",
+            fp64_planes=16, cpu_crop=16),
+    }
+
+
+DEFAULT_WORKLOAD = "voronoi2d-1024"
 
 
 def parse():
@@ -45,6 +97,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["auto", "fp64", "fp32", "gated"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time the headline path only (no other paths, e2e or CPU baseline): for profiler runs")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=["voronoi2d-1024", "halfsine3d-256", "mixed2d-2048", "mixed3d-512-r3"])
     return ap.parse_args()
 
 
@@ -64,10 +120,11 @@ def run_reference(args, world, rank):
     import numpy as np
 
     import oracle
-    import workloads
-    crop = 128
-    U = np.ascontiguousarray(workloads.voronoi_2d(N_GRID, k=64, seed=2).numpy()[:, :crop, :crop])
-    o = oracle.Oracle([crop, crop], dim=2, R=RADIUS, bc="outflow")
+    W = _workloads()[args.workload]
+    crop = W.cpu_crop
+    U = W.make("cpu").numpy()
+    U = np.ascontiguousarray(U[:, :crop, :crop] if W.dims == 2 else U[:, :crop, :crop, :crop])
+    o = oracle.Oracle([crop] * W.dims, dim=W.dims, R=W.R, bc=W.bc)
     for _ in range(args.warmup):
         o.step(U, CFL)
     t0 = time.perf_counter()
@@ -75,15 +132,16 @@ def run_reference(args, world, rank):
     for _ in range(args.steps):
         Ur, _ = o.step(Ur, CFL)
     el = time.perf_counter() - t0
-    value = crop * crop * 3 * args.steps / el
+    value = crop ** W.dims * 3 * args.steps / el
+    shape = "x".join([str(crop)] * W.dims)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "radius": RADIUS,
-                   "sample": f"{crop}x{crop} corner crop of the workload per step"},
+        "config": {"workload": W.desc, "grid": W.n, "radius": W.R,
+                   "sample": f"{shape} corner crop of the workload per step"},
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"SSP-RK3 steps of a {crop}x{crop} crop, single-threaded C oracle"},
+                         "sample": f"SSP-RK3 steps of a {shape} crop, single-threaded C oracle"},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -166,27 +224,23 @@ def time_steps(g, U, steps, stream, flush_buf):
     return total  # ms
 
 
-GATE_PARAMS = os.path.join(ROOT, "paper_2401_16543_gb300", "gate_params_2d.npy")
-GATE_THRESHOLD = 0.8
-
-
-def make_solver(path, U_dev):
+def make_solver(W, path, n=None):
     import numpy as np
 
     from paper_2401_16543_gb300 import KFVM
-    g = KFVM([N_GRID, N_GRID], dims=2, radius=RADIUS, bc="outflow")
+    g = KFVM(list(n or W.n), dims=W.dims, radius=W.R, bc=W.bc)
     if path in ("fp32", "gated"):
         g.set_option("precision", 32)
     if path == "gated":
-        g.gate_set_params(np.load(GATE_PARAMS))
+        g.gate_set_params(np.load(W.gate_path()))
         g.set_option("gate_threshold", GATE_THRESHOLD)
         g.set_option("recon", 2)
     return g
 
 
-def measure_path(path, U0, steps, warmup, stream, flush_buf, profile_kernel):
+def measure_path(W, path, U0, steps, warmup, stream, flush_buf, n=None):
     import torch
-    g = make_solver(path, U0)
+    g = make_solver(W, path, n)
     U = U0.clone()
     with torch.cuda.stream(stream):
         for _ in range(warmup):
@@ -220,24 +274,24 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import paper_2401_16543_gb300 as pkg
-    import workloads
     pkg.load()
+    W = _workloads()[args.workload]
     dev = torch.device("cuda", local)
-    U0 = workloads.voronoi_2d(N_GRID, k=64, seed=2, device=dev).contiguous()
-    ncell = N_GRID * N_GRID
+    U0 = W.make(dev).contiguous()
+    ncell = W.ncell
     stream = torch.cuda.Stream(device=dev)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     path = args.path
     if path == "auto":
-        path = "gated" if os.path.exists(GATE_PARAMS) else "fp32"
+        path = "gated" if W.has_gate() else "fp32"
     sampler = ClockSampler(torch.cuda.current_device() if world == 1 else local)
     sampler.start()
     # ---- headline path, resident inputs ----
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    g, ms, prof, launches, g_final_state = measure_path(path, U0, args.steps, args.warmup, stream, flush_buf, None)
+    g, ms, prof, launches, g_final_state = measure_path(W, path, U0, args.steps, args.warmup, stream, flush_buf)
     torch.cuda.synchronize()
     if dist is not None:
         t = torch.tensor([ms], device=dev)
@@ -250,12 +304,33 @@ def main():
     # ---- the other paths on the same workload (plain FP64 is the metric's reference) ----
     others = {}
     for other in ("fp64", "fp32", "gated"):
-        if other == path or (other == "gated" and not os.path.exists(GATE_PARAMS)):
+        if args.headline_only or other == path or (other == "gated" and not W.has_gate()):
             continue
         k = max(3, args.steps // 4)
-        _, mso, _, _, _ = measure_path(other, U0, k, 2, stream, flush_buf, None)
-        others[other] = {"value": world * ncell * 3 * k / (mso * 1e-3), "ms_per_step": mso / k, "steps": k}
+        Uo0, n_o, note = U0, None, None
+        if other == "fp64" and W.fp64_planes:
+            # the plain FP64 path on the first z-planes of the same state (seconds per stage at full size)
+            Uo0 = U0[:, :W.fp64_planes].contiguous()
+            n_o = W.n[:2] + [W.fp64_planes]
+            note = f"first {W.fp64_planes} z-planes of the state ({W.n[0]}x{W.n[1]}x{W.fp64_planes} cells)"
+            k = 1
+        _, mso, _, _, _ = measure_path(W, other, Uo0, k, 1 if other == "fp64" else 2, stream, flush_buf, n_o)
+        cells = ncell if n_o is None else n_o[0] * n_o[1] * n_o[2]
+        others[other] = {"value": world * cells * 3 * k / (mso * 1e-3), "ms_per_step": mso / k, "steps": k}
+        if note:
+            others[other]["sample"] = note
+        del Uo0
     fp64 = others.get("fp64", {"value": value, "ms_per_step": ms / args.steps})
+
+    if args.headline_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                              "config": {"name": W.name, "path": path}, "gpu_launches": launches,
+                              "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()}, "headline_only": True}))
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     # ---- end to end through the C ABI with host buffers ----
     Uh = U0.cpu().pin_memory()
@@ -285,7 +360,7 @@ def main():
     kern = "recon64" if path == "fp64" else "recon32"
     n_launch, kms = prof.get(kern, (0, 0.0))
     mode = "weno" if path in ("fp64", "fp32") else "gated"
-    flops = algo_flops_per_cell(2, RADIUS, "weno") * ncell
+    flops = algo_flops_per_cell(W.dims, W.R, "weno") * ncell
     smooth_frac = None
     if path == "gated":
         # WENO cells at WENO cost, gated cells at the linear reconstruction's cost, averaged over
@@ -294,12 +369,12 @@ def main():
         for Us in (U0, g_final_state):
             fr.append(float(g.gate_mask(Us).float().mean().item()))
         smooth_frac = sum(fr) / len(fr)
-        flops = ncell * (smooth_frac * algo_flops_per_cell(2, RADIUS, "linear")
-                         + (1 - smooth_frac) * algo_flops_per_cell(2, RADIUS, "weno"))
+        flops = ncell * (smooth_frac * algo_flops_per_cell(W.dims, W.R, "linear")
+                         + (1 - smooth_frac) * algo_flops_per_cell(W.dims, W.R, "weno"))
     peak_flops = pkg.measure_fma_peak(64 if path == "fp64" else 32)
     achieved = flops / (kms / n_launch * 1e-3) if n_launch else 0.0
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"{kern}_traffic.txt")
+    tfile = os.path.join(ROOT, "profiles", f"{kern}_{W.name}_traffic.txt")
     if os.path.exists(tfile):
         for line in open(tfile):
             if line.startswith("traffic_bytes_per_launch"):
@@ -317,13 +392,22 @@ def main():
         import numpy as np
 
         import oracle
-        Un = U0.cpu().numpy()
-        o = oracle.Oracle([N_GRID, N_GRID], dim=2, R=RADIUS, bc="outflow")
+        if W.name == DEFAULT_WORKLOAD:
+            Un, shape = U0.cpu().numpy(), W.n
+        else:
+            c = W.cpu_crop
+            Un = U0[:, :c, :c].cpu().numpy() if W.dims == 2 else U0[:, :c, :c, :c].cpu().numpy()
+            shape = [c] * W.dims
+        o = oracle.Oracle(list(shape), dim=W.dims, R=W.R, bc=W.bc)
         t0 = time.perf_counter()
-        o.step(Un, CFL)
+        o.step(np.ascontiguousarray(Un), CFL)
         el = time.perf_counter() - t0
-        cpu = {"value": ncell * 3 / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-               "sample": "one SSP-RK3 step (3 RK stages) of the full 1024x1024 workload, single-threaded C oracle"}
+        cells = 1
+        for v in shape:
+            cells *= v
+        cpu = {"value": cells * 3 / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"one SSP-RK3 step (3 RK stages) of {'x'.join(map(str, shape))} cells of the workload, "
+                         "single-threaded C oracle"}
 
     if rank == 0:
         line = {
@@ -331,8 +415,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "gated": "f32+bf16"}[path],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "radius": RADIUS, "path": path,
-                       "gate": ({"params": "paper_2401_16543_gb300/gate_params_2d.npy",
+            "config": {"workload": W.desc, "name": W.name, "grid": W.n, "radius": W.R, "path": path,
+                       "gate": ({"params": f"paper_2401_16543_gb300/{W.gate}",
                                  "threshold": GATE_THRESHOLD} if path == "gated" else None),
                        "l2": "flushed between timed steps (256 MB write outside the step events)",
                        "replicas": world},

@@ -200,7 +200,7 @@ kfvm_status kfvm_sync_status(kfvm_ctx* ctx, void* stream);
 /* Network: in -> 32 -> 32 -> 1, ReLU hidden layers, sigmoid output; the input
  * is the radius-2 full stencil of rho and p (cell-average pressure), each as
  * deviations from the central value divided by d = max(max |deviation|,
- * 1e-5 |central value|): 2*|S0(R=2)| values (26 in 2D, 66 in 3D).  In 3D two
+ * 1e-4 |central value|): 2*|S0(R=2)| values (26 in 2D, 66 in 3D).  In 3D two
  * more inputs, m/(m + d) with m = max |deviation| over the shell
  * 4 < |o|^2 <= 9 of rho and of p, let the network see what a radius-3
  * reconstruction reads (zero when the radius is 2): in = 68 in 3D.
@@ -213,10 +213,10 @@ kfvm_status kfvm_gate_get_params(kfvm_ctx* ctx, float* host_params, size_t count
 
 /* Gate inputs and WENO-AO training labels of every cell of U:
  * X (device, float32 [ncell][in]) and y (device, float32 [ncell]) with
- * y = 1 when every linearized-primitive component either has
- * omega_0/gamma_0 >= 1 - tau (the cell's own WENO-AO weights at the
- * context's radius say it is smooth) or varies over S0 by at most 1e-6 of its
- * scale (rho, sound speed, p), else 0.  The deltas are formed in float64. */
+ * y = 1 when the density and the pressure components of the linearized
+ * primitive variables each either have omega_0/gamma_0 >= 1 - tau (the cell's
+ * own WENO-AO weights at the context's radius say it is smooth) or vary over
+ * S0 by at most 1e-4 of their scale, else 0.  The deltas are formed in float64. */
 kfvm_status kfvm_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, void* stream);
 
 /* The smooth mask the gated step computes from U with the loaded network

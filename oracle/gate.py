@@ -8,18 +8,23 @@ module states, in plain FP64 numpy, what the GPU's gate computes:
 * ``features``: for each cell, the radius-2 full stencil of rho and of the
   cell-average pressure p = (gamma-1)(E - |m|^2/(2 rho)), each block as
   deviations from the central cell's value divided by
-  d = max(max |deviation|, 1e-5 |central value|) (+1e-30): exactly zero on
-  constant data, unchanged by a common scaling of the state (the 1e-5 floor keeps
-  the ~1e-7 rounding of a float32 pressure below 0.05 in a flat block).  In 3D two more
+  d = max(max |deviation|, 1e-4 |central value|) (+1e-30): exactly zero on
+  constant data, unchanged by a common scaling of the state; the 1e-4 floor is
+  the amplitude below which the labels call a component smooth, so a variation
+  that small shows as a small input (and the ~1e-7 rounding of a float32
+  pressure stays below 0.01).  In 3D two more
   inputs describe the shell 4 < |o|^2 <= 9 that a radius-3 reconstruction also
   reads (the radius-2 block cannot see a jump three cells away): per block
   m / (m + d) with m = max |deviation| over the shell, in [0, 1); they are zero
   unless the reconstruction radius is 3.
-* ``labels``: 1 when every linearized primitive component is smooth by the
-  cell's own WENO-AO weights (omega_0/gamma_0 >= 1 - tau; Eqs. 24-25 of the
-  paper, from the oracle's reconstruction) or varies over the radius-R stencil
-  by less than 1e-6 of its scale (rho~, p~, sound speed for velocities), where
-  WENO-AO and the linear reconstruction cannot differ by more than that.
+* ``labels``: 1 when the density and pressure components of the linearized
+  primitive variables (the two quantities the features describe) are both
+  smooth by the cell's own WENO-AO weights (omega_0/gamma_0 >= 1 - tau; Eqs.
+  24-25 of the paper, from the oracle's reconstruction) or vary over the
+  radius-R stencil by less than 1e-4 of their scale (rho~, p~), where WENO-AO
+  and the linear reconstruction cannot differ by more than that (truncation
+  errors of a smooth flow stay below it, and WENO-AO weights of such noise say
+  nothing about smoothness).
 * ``forward`` / ``loss_and_grad``: the MLP NIN -> 32 -> 32 -> 1 (ReLU, ReLU,
   sigmoid) and the gradient of its mean binary cross-entropy by backprop.
   Parameter packing: W1 [32][NIN], b1 [32], W2 [32][32], b2 [32], W3 [32], b3.
@@ -128,7 +133,7 @@ def features(U, dim: int, bc="periodic", gamma: float = 1.4, R: int = 2) -> np.n
         A = np.stack([column(field, o) for o in s0], axis=1)
         c = A[:, centre:centre + 1]
         dev = A - c
-        scale = np.maximum(np.abs(dev).max(axis=1, keepdims=True), 1e-5 * np.abs(c) + 1e-30)
+        scale = np.maximum(np.abs(dev).max(axis=1, keepdims=True), 1e-4 * np.abs(c) + 1e-30)
         out.append(dev / scale)
         if dim == 3:
             if R >= 3:
@@ -178,14 +183,17 @@ def linprim_amplitude(U, dim: int, R: int, bc="periodic", gamma: float = 1.4):
     return amp / scale
 
 
+LABEL_VARS = (0, -1)  # density and pressure components of the linearized primitive variables
+
+
 def labels_from_omega(omega, dim: int, tau: float, amplitude=None):
     """Labels from the oracle's weights omega [nq, nv, *grid] and (optionally) linprim_amplitude;
-    returns (y, worst ratio over the components that count)."""
+    returns (y, worst ratio over the components that count: density and pressure)."""
     g0 = stencils.linear_weights(dim)[0]
     ratio = (omega[0] / g0).reshape(omega.shape[1], -1)
     if amplitude is not None:
-        ratio = np.where(amplitude <= 1e-6, 1.0, ratio)
-    worst = ratio.min(axis=0)
+        ratio = np.where(amplitude <= 1e-4, 1.0, ratio)
+    worst = ratio[list(LABEL_VARS)].min(axis=0)
     return (worst >= 1.0 - tau).astype(np.float64), worst
 
 

@@ -10,7 +10,7 @@
 //
 // Network: NIN -> 32 -> 32 -> 1 (ReLU, ReLU, sigmoid).  Input: the radius-2
 // full stencil of rho and of the cell-average pressure, each as deviations from
-// the central cell divided by max(max |deviation|, 1e-5 |central value|), so a
+// the central cell divided by max(max |deviation|, 1e-4 |central value|), so a
 // feature vector describes the shape of the data and not its amplitude (as the
 // WENO weights do) and is exactly zero on constant data in any precision.  Matrix products run on the tensor cores with
 // mma.sync.m16n8k16 (BF16 operands, FP32 accumulation) on 32-row warp tiles;

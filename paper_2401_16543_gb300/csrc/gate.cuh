@@ -134,15 +134,16 @@ __device__ __forceinline__ void load_pack(const Pack<D>* __restrict__ src, Pack<
 }
 
 // Normalise a feature block in place: deviations from the central value divided by
-// d = max(max |deviation|, 1e-5 |central value|) (+1e-30); returns d.  The floor keeps the
-// rounding of a float32 pressure (~1e-7 of E) below 0.05 in a block that is flat.
+// d = max(max |deviation|, 1e-4 |central value|) (+1e-30); returns d.  The floor is the
+// amplitude below which the training labels call a component smooth, so smaller variations
+// show as small inputs (and the rounding of a float32 pressure stays below 0.01).
 template <int N0, int C>
 __device__ __forceinline__ float normalise_block(float* v) {
   const float vc = v[C];
   float mx = 0.0f;
 #pragma unroll
   for (int l = 0; l < N0; ++l) mx = fmaxf(mx, fabsf(v[l] - vc));
-  const float d = fmaxf(mx, 1e-5f * fabsf(vc) + 1e-30f);
+  const float d = fmaxf(mx, 1e-4f * fabsf(vc) + 1e-30f);
   const float inv = __frcp_rn(d);
 #pragma unroll
   for (int l = 0; l < N0; ++l) v[l] = (v[l] - vc) * inv;

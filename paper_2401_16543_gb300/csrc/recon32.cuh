@@ -495,11 +495,11 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
 }
 
 // Training labels of the learned gate, from the cell's own WENO-AO weights
-// (Eqs. 22, 24, 25): y = 1 when every linearized primitive component is smooth
-// by the weights (omega_0/gamma_0 >= thresh = 1 - tau) or varies over the
-// stencil by less than 1e-6 of its scale (rho~ for density, p~ for pressure,
-// the sound speed for velocities), where WENO-AO and the linear
-// reconstruction differ by less than that; else 0.  The lin-prim deltas are
+// (Eqs. 22, 24, 25): y = 1 when the density and the pressure components of the
+// linearized primitive variables (the quantities the gate's inputs describe)
+// are both smooth by the weights (omega_0/gamma_0 >= thresh = 1 - tau) or vary
+// over the stencil by less than 1e-4 of their scale (rho~, p~), where WENO-AO
+// and the linear reconstruction differ by less than that; else 0.  The lin-prim deltas are
 // formed in float64 from the float64 state (a float32 shadow would leave
 // rounding noise of ~1e-7 of E in components that are constant, and the
 // weights of noise are random); the indicators then run in float32 as in the
@@ -616,10 +616,11 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS) label_kernel(GridArgs a, c
   const Ref64<D, R> r(smem64l, c, a.gamma);
   float worst = 1.0f;
 #pragma unroll 1
-  for (int v = 0; v < NV; ++v) {
+  for (int iv = 0; iv < 2; ++iv) {
+    const int v = iv == 0 ? 0 : NV - 1;  // density, pressure
     float g[N0];
     const float amp = load_deltas64<D, R>(r, smem64l, c, v, g, std::make_integer_sequence<int, N0>{});
-    if ((double)amp <= 1e-6 * r.scale_of(v)) continue;  // negligible variation: smooth whatever the weights
+    if ((double)amp <= 1e-4 * r.scale_of(v)) continue;  // negligible variation: smooth whatever the weights
     float beta[NQ];
     all_betas<D, R>(W, g, beta, std::make_integer_sequence<int, NQ>{});
     worst = fminf(worst, omega0_ratio<D, NQ>(beta, a.epsf));

@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(TH, 3) recon33_kernel(GridArgs a, int mode, co
 }
 
 // Training labels of the learned gate for d = 3, R = 3: the rule of r32::label_kernel
-// (float64 lin-prim deltas, float32 indicators), with the rolled contraction above.
+// (density and pressure components; float64 lin-prim deltas, float32 indicators), with the
+// rolled contraction above.
 __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* __restrict__ U, float* __restrict__ y,
                                                      float thresh, const float4* __restrict__ Wt) {
   extern __shared__ double smem33l[];
@@ -330,12 +331,13 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
   const r32::Ref64<3, 3> r(smem33l, c, a.gamma);
   float worst = 1.0f;
 #pragma unroll 1
-  for (int v = 0; v < NV; ++v) {
+  for (int iv = 0; iv < 2; ++iv) {
+    const int v = iv == 0 ? 0 : NV - 1;  // density, pressure
     auto delta = [&](int o) { return r.delta(smem33l, o, v); };
     float amp = 0.0f;
 #pragma unroll 4
     for (int k = 0; k < c_pairs.start[1]; ++k) amp = fmaxf(amp, fabsf(delta(c + c_pairs.off[k])));
-    if ((double)amp <= 1e-6 * r.scale_of(v)) continue;
+    if ((double)amp <= 1e-4 * r.scale_of(v)) continue;
     float beta[NQ];
     betas(c, delta, Wt, beta);
     worst = fminf(worst, r32::omega0_ratio<3, NQ>(beta, a.epsf));

@@ -13,16 +13,18 @@ runs of the two 2D workloads:
 From the pooled pairs, `--pairs` are drawn with seed 41 (the last 5% held out);
 the network is trained by kfvm_gate_train_step (BF16 forward/backward on the
 tensor cores, FP32 accumulation, Adam on FP32 masters; 20 epochs of batches of
-16384, learning rate 3e-3 stepped down to 1e-3 and 3e-4).  The result is written
+2048, learning rate 1e-3 stepped down to 3.3e-4 and 1e-4: smaller batches than
+the GPU could take give more steps and a better-separated (more confident)
+network at the same data).  The result is written
 as float32 .npy in the packing of kfvm_gate_set_params.
 
     python -m paper_2401_16543_gb300.train_gate --out paper_2401_16543_gb300/gate_params_2d.npy
 
 3D (radius-3 labels; the radius-2 stencils of rho and p plus the two radius-3 shell
-inputs): pairs from a 48^3 smooth run and two 128^3 runs (generate_3d), written to
-gate_params_3d.npy:
+inputs): pairs from smooth runs on 24^3 ... 64^3 cells and two 128^3 Voronoi runs
+(generate_3d), all of them used, written to gate_params_3d.npy:
 
-    python -m paper_2401_16543_gb300.train_gate --dims 3 --radius 3
+    python -m paper_2401_16543_gb300.train_gate --dims 3 --radius 3 --pairs 36000000
 """
 from __future__ import annotations
 
@@ -82,7 +84,7 @@ def generate(tau: float, voronoi_n: int = 1024, voronoi_steps: int = 200, every:
 
 def generate_3d(tau: float, n: int = 128, steps: int = 30, every: int = 6, R: int = 3, device="cuda"):
     """Pooled (X, y) from 3D runs at radius R, FP32 WENO-AO everywhere, CFL 0.4:
-    the smooth translation on 48^3 cells (periodic, every step to t = 0.05), the
+    the smooth translation on 24^3 ... 64^3 cells (periodic, to t = 0.05), the
     half-sine / half-Voronoi state (16 regions in x >= 1/2, seed 3, periodic) and the
     mixed state (16 regions, each smooth or constant, seed 5, outflow) on n^3 cells,
     features and labels of every `every`-th of `steps` SSP-RK3 steps."""
@@ -91,16 +93,21 @@ def generate_3d(tau: float, n: int = 128, steps: int = 30, every: int = 6, R: in
     import workloads
     from paper_2401_16543_gb300 import KFVM
     Xs, ys = [], []
-    g = KFVM([48, 48, 48], dims=3, radius=R, bc="periodic")
-    g.set_option("precision", 32)
-    U = workloads.sine_3d(48, R=R, device=device).contiguous()
-    t = 0.0
-    while t < 0.05:
-        X, y = g.gate_features(U, tau)
-        Xs.append(X)
-        ys.append(y)
-        t += g.step(U, 0.4, 0.05 - t)
-    del U, g
+    # the smooth translation at several resolutions (the sine's phase step per cell changes the
+    # shape of a normalised stencil); snapshots thinned so that each resolution gives ~1-2 M pairs
+    for ns, every_s in ((24, 1), (32, 1), (48, 2), (64, 4)):
+        g = KFVM([ns] * 3, dims=3, radius=R, bc="periodic")
+        g.set_option("precision", 32)
+        U = workloads.sine_3d(ns, R=R, device=device).contiguous()
+        t, k = 0.0, 0
+        while t < 0.05:
+            if k % every_s == 0:
+                X, y = g.gate_features(U, tau)
+                Xs.append(X)
+                ys.append(y)
+            t += g.step(U, 0.4, 0.05 - t)
+            k += 1
+        del U, g
     for make, bc in ((lambda: workloads.half_sine_voronoi_3d(n, k=16, seed=3, R=R, device=device), "periodic"),
                      (lambda: workloads.mixed_voronoi(3, n, 16, seed=5, R=R, device=device), "outflow")):
         g = KFVM([n, n, n], dims=3, radius=R, bc=bc)
@@ -174,8 +181,8 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--pairs", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=20)
-    ap.add_argument("--batch", type=int, default=16384)
-    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--tau", type=float, default=0.5)
     args = ap.parse_args()
     t0 = time.time()

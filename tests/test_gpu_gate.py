@@ -57,7 +57,7 @@ def test_features_and_labels(kfvm, idx):
     Xg = X.cpu().numpy()
     Xr = ogate.features(U0.numpy(), 2, bc)
     # blocks whose relative variation is far above float32 rounding agree to 1e-3; blocks that are
-    # flat to ~1e-7 relative hold float32 rounding noise scaled by the 1e-5 floor
+    # flat to ~1e-7 relative hold float32 rounding noise scaled by the 1e-4 floor
     U = U0.numpy()
     for blk in range(2):
         sl = slice(13 * blk, 13 * blk + 13)
@@ -72,7 +72,7 @@ def test_features_and_labels(kfvm, idx):
     amp = ogate.linprim_amplitude(U0.numpy(), 2, 2, bc)
     yr, worst = ogate.labels_from_omega(om, 2, 0.5, amp)
     # cells whose decision sits at a threshold (weights or amplitude) may fall either way in float32
-    far = (np.abs(worst - 0.5) > 1e-3) & (np.abs(np.log10(np.maximum(amp, 1e-30)) + 6).min(axis=0) > 0.05)
+    far = (np.abs(worst - 0.5) > 1e-3) & (np.abs(np.log10(np.maximum(amp[[0, -1]], 1e-30)) + 4).min(axis=0) > 0.05)
     assert np.array_equal(y.cpu().numpy()[far], yr[far])
     assert far.mean() > 0.9
 
@@ -252,3 +252,21 @@ def test_3d_features_with_shell_match_oracle(kfvm, R):
         else:
             cells = slice(None) if blk == 0 else big
             assert np.abs(Xg[cells, 66 + blk] - Xr[cells, 66 + blk]).max() <= 1e-3
+
+
+@pytest.mark.parametrize("R", [2, 3])
+def test_3d_labels_match_oracle(kfvm, R):
+    """3D training labels (float64 deltas, float32 indicators) against the oracle's FP64 labels, on the
+    cells whose decision is not at a threshold."""
+    n = (10, 9, 8)
+    U0 = workloads.mixed_voronoi(3, 10, 5, seed=29)[:, :n[2], :n[1], :n[0]].contiguous()
+    g = kfvm.KFVM(list(n), dims=3, radius=R, bc="outflow")
+    _, y = g.gate_features(U0.cuda(), tau=0.5)
+    o = oracle.Oracle(list(n), dim=3, R=R, bc="outflow")
+    _, om = o.reconstruct(U0.numpy(), with_omega=True)
+    amp = ogate.linprim_amplitude(U0.numpy(), 3, R, "outflow")
+    yr, worst = ogate.labels_from_omega(om, 3, 0.5, amp)
+    far = (np.abs(worst - 0.5) > 1e-3) & (np.abs(np.log10(np.maximum(amp[[0, -1]], 1e-30)) + 4).min(axis=0) > 0.05)
+    assert far.mean() > 0.9
+    assert np.array_equal(y.cpu().numpy()[far], yr[far])
+    assert 0.05 < yr.mean() < 0.95

@@ -81,7 +81,7 @@ def test_features_match_direct_stencil_loop():
             c = s0.index((0, 0, 0))
             for v in (rho, p):
                 d = v - v[c]
-                want.append(d / max(np.abs(d).max(), 1e-5 * abs(v[c]) + 1e-30))
+                want.append(d / max(np.abs(d).max(), 1e-4 * abs(v[c]) + 1e-30))
             assert np.allclose(f[j * n + i], np.concatenate(want), atol=1e-13)
 
 
@@ -119,7 +119,7 @@ def test_3d_shell_features_see_a_jump_three_cells_away():
             else:
                 val = lambda o: 0.4 * (at(o, 4) - 0.5 * sum(at(o, 1 + q) ** 2 for q in range(3)) / at(o, 0))  # noqa: E731
             vc = val((0, 0, 0))
-            d = max(max(abs(val(o) - vc) for o in s0), 1e-5 * abs(vc) + 1e-30)
+            d = max(max(abs(val(o) - vc) for o in s0), 1e-4 * abs(vc) + 1e-30)
             ms = max(abs(val(o) - vc) for o in sh)
             assert abs(fv[(k * m + j) * m + i, 66 + blk] - ms / (ms + d)) <= 1e-13
 
@@ -159,3 +159,20 @@ def test_amplitude_clause_marks_constant_and_tiny_variations_smooth():
     _, om = oracle.Oracle([n, n], dim=2, R=2, bc="outflow").reconstruct(V, with_omega=True)
     y, _ = gate.labels_from_omega(om, 2, 0.5, gate.linprim_amplitude(V, 2, 2, "outflow"))
     assert y.min() == 0.0
+
+
+def test_labels_count_density_and_pressure_only():
+    """The label looks at the density and pressure components of the linearized primitive variables
+    (what the features describe): a velocity component whose weights say non-smooth does not change
+    it, the density or the pressure component does."""
+    g = oracle.stencils.linear_weights(2)
+    nq, nv, ncell = len(g), 4, 3
+    om = np.tile(np.asarray(g)[:, None, None], (1, nv, ncell))  # omega = gamma: smooth everywhere
+    bad = np.zeros(nq)
+    bad[0], bad[1] = 0.1, 0.9  # omega_0 / gamma_0 = 0.125
+    om[:, 1, 0] = bad  # cell 0: u non-smooth
+    om[:, 0, 1] = bad  # cell 1: rho non-smooth
+    om[:, 3, 2] = bad  # cell 2: p non-smooth
+    y, worst = gate.labels_from_omega(om, 2, 0.5)
+    assert list(y) == [1.0, 0.0, 0.0]
+    assert worst[0] == 1.0 and abs(worst[1] - 0.125) < 1e-15
