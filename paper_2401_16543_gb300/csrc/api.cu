@@ -288,6 +288,7 @@ kfvm_status kfvm_init(kfvm_ctx** out, const kfvm_grid* g, int dims, int radius, 
   // float32 weights: the packed table, or for d = 3, R = 3 the padded row table of recon32_33
   if (e == cudaSuccess)
     e = dalloc(&c->d_w32, (dims == 3 && radius == 3) ? recon33_table_floats() : c->wcount);
+  if (e == cudaSuccess && dims == 3 && radius == 3) e = cudaMalloc(&c->d_w33tc, recon33_tc_image_bytes());
   // Riemann-state buffer: the whole grid if it fits in 8 GiB (float64), else 3D z-slabs
   // of S planes plus one plane on each side (kfvm_step loops over the slabs)
   {
@@ -328,6 +329,7 @@ void kfvm_destroy(kfvm_ctx* c) {
   for (cudaEvent_t e : c->prof_free) cudaEventDestroy(e);
   cudaFree(c->d_w64);
   cudaFree(c->d_w32);
+  cudaFree(c->d_w33tc);
   cudaFree(c->d_faces);
   cudaFree(c->d_flux);
   cudaFree(c->d_stage);
@@ -370,6 +372,11 @@ kfvm_status kfvm_build_weights(kfvm_ctx* ctx, void* stream) {
   else
     for (size_t i = 0; i < ctx->wcount; ++i) w32[i] = (float)ctx->w_host[i];
   KFVM_TRY(cudaMemcpy(ctx->d_w32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
+  if (ctx->d_w33tc) {
+    std::vector<unsigned char> img(recon33_tc_image_bytes(), 0);
+    recon33_tc_fill_image(ctx->w_host.data(), img.data());
+    KFVM_TRY(cudaMemcpy(ctx->d_w33tc, img.data(), img.size(), cudaMemcpyHostToDevice));
+  }
   ctx->weights_built = true;
   return KFVM_OK;
 }
@@ -405,6 +412,9 @@ kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double v) {
   } else if (k == "eps") {
     if (!(v > 0)) return KFVM_ERR_ARG;
     ctx->eps = v;
+  } else if (k == "tensor_cores") {
+    if (v != 0 && v != 1) return KFVM_ERR_ARG;
+    ctx->tensor_cores = (int)v;
   } else if (k == "slab_planes") {
     // split 3D steps into z-slabs of this many planes (at most what the buffer was sized for)
     if (!(v >= 1) || ctx->dims != 3) return KFVM_ERR_ARG;

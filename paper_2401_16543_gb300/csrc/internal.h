@@ -52,6 +52,7 @@ struct kfvm_ctx {
   int degrees[kfvm::kMaxNQ] = {0};
   // options
   int precision = 64, recon = 0, riemann = 0, positivity = 1;
+  int tensor_cores = 1;  // d = 3, R = 3 FP32 contraction on tcgen05 (0: the CUDA-core kernel)
   double kappa = 0.1, eta = 0.0, eps = 1e-40, gate_threshold = 0.5;
   // weights
   size_t wcount = 0;
@@ -59,6 +60,7 @@ struct kfvm_ctx {
   std::vector<double> w_host;  // float64 tables (kernel-parameter copies are made from these)
   double* d_w64 = nullptr;
   float* d_w32 = nullptr;
+  void* d_w33tc = nullptr;       // d = 3, R = 3: FP16 hi/lo weight image of the tensor-core kernel
   // scratch owned by the library
   void* d_faces = nullptr;       // F * nv * ncell values (float64 or float32)
   double* d_flux = nullptr;      // face-averaged fluxes, per direction nv * (n_d + 1) * prod(n_other)
@@ -104,6 +106,8 @@ cudaError_t launch_recon64(kfvm_ctx* ctx, const double* U, double* faces, cudaSt
 // d = 3, R = 3 FP32 weights: padded row table (floats) and its fill from the float64 tables
 size_t recon33_table_floats();
 void recon33_fill_table(const double* w, float* out);
+size_t recon33_tc_image_bytes();
+void recon33_tc_fill_image(const double* w, unsigned char* out);
 cudaError_t launch_recon32(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st,
                            int zf_first = 0, int zf_count = 0);
 cudaError_t launch_face_flux(kfvm_ctx* ctx, const void* faces, cudaStream_t st);

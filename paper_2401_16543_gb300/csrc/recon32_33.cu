@@ -18,8 +18,13 @@
 //     states), which overwrites them: no shared-memory copy of 270 values per cell.
 // The gated mode evaluates the learned gate on the tile (features of the radius-2
 // stencil, MLP on the tensor cores) and compacts the WENO cells as recon32 does.
+#include <cuda_fp16.h>
+
+#include <cmath>
+
 #include "internal.h"
 #include "recon32.cuh"
+#include "tc.cuh"
 
 namespace kfvm {
 namespace r33 {
@@ -127,10 +132,10 @@ __device__ __forceinline__ void betas(int cc, Delta delta, const float4* __restr
 
 // stage the float32 shadow of a tile (+ halo 3) and its float32 pressures
 __device__ __forceinline__ void stage_tile(const GridArgs& a, const float* __restrict__ S, float* sm, float* sp,
-                                           int x0, int y0, int z0) {
+                                           int x0, int y0, int z0, int nthreads = TH) {
   const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
   const float gm1 = a.gammaf - 1.0f;
-  for (int i = threadIdx.x; i < SN; i += TH) {
+  for (int i = threadIdx.x; i < SN; i += nthreads) {
     const int sx = i % T::SX, sy = (i / T::SX) % T::SY, sz = i / (T::SX * T::SY);
     const int gx = map_index(x0 + sx, a.n[0], a.bc[0][0], a.bc[0][1]);
     const int gy = map_index(y0 + sy, a.n[1], a.bc[1][0], a.bc[1][1]);
@@ -345,6 +350,373 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
   y[cell] = worst >= thresh ? 1.0f : 0.0f;
 }
 
+// ===========================================================================
+// Tensor-core variant (tcgen05): the contraction as a GEMM per (tile of 128 cells, variable).
+//
+// Rows of A are the 128 cells of a tile (M = 128, one TMEM lane per cell); its K
+// columns are the (stencil, cell) pairs, each stencil's block padded to a multiple
+// of 16 (128 + 48 + 6 x 32 = 368, 23 MMA k-steps).  A holds the lin-prim deltas
+// divided by a per-(cell, variable) power of two s >= max |delta| over S0, split
+// into two FP16 halves (hi + lo); B holds the weights split the same way (each
+// output column scaled by a power of two).  Three kind::f16 MMAs per k-step
+// (hi.hi + hi.lo + lo.hi, FP32 accumulation in TMEM) carry ~22 bits, i.e. the
+// accuracy of the FP32 contraction.
+//   pass 1: derivative values of every stencil, D1 = 8 blocks of 32 TMEM columns
+//           (stencil q's k-steps accumulate into columns 32 q ...), read back per
+//           cell -> beta_q -> WENO-AO coefficients (as in the CUDA-core kernel);
+//   pass 2: A rebuilt with each stencil's block times that cell's coefficient, so
+//           that all 23 k-steps accumulate the blended face values into one
+//           D2 of 64 columns (54 used).
+// Tiles whose cells are all linear (gated modes) skip pass 1 and run the 8 k-steps
+// of S0 only.  The CTA is persistent (one per SM): B (138 KB, FP16 hi/lo) is
+// loaded into shared memory once; 256 threads build A chunks (cell r = t % 128,
+// half h = t / 128 of each 16-wide k-step) in a ring of 4 buffers, thread 0 issues
+// the MMAs and commits each buffer back to its mbarrier.  Every wait has an
+// iteration limit; on expiry the kernel raises the timeout flag and stops.
+// ===========================================================================
+namespace tcg {
+
+constexpr int KS = 23;                     // k-steps of 16
+constexpr int KT = KS * 16;                // padded K = 368
+constexpr int TCT = 256;                   // threads per CTA
+constexpr int NB = 4;                      // A ring buffers
+constexpr int B1_BLOCK = 2048;             // pass-1 B block: 32 x 16 FP16, hi + lo
+constexpr int B2_BLOCK = 4096;             // pass-2 B block: 64 x 16 FP16, hi + lo
+constexpr int B1_BYTES = KS * B1_BLOCK;
+constexpr int B2_BYTES = KS * B2_BLOCK;
+constexpr int CS_FLOATS = NQ * 32 + 64;    // column scales (pass 1 per stencil, pass 2)
+constexpr int B_BYTES = B1_BYTES + B2_BYTES + CS_FLOATS * 4;
+constexpr int A_BUF = 8192;                // 128 x 16 FP16, hi + lo
+constexpr int WAIT_LIMIT = 1 << 22;
+
+struct KMap {
+  int kq[KS];       // stencil of each k-step
+  int first[KS];    // 1 on the first k-step of a stencil
+  int off[KT];      // tile offset of each padded K column; kPad for padding
+};
+constexpr int kPad = 1 << 28;
+
+constexpr KMap make_kmap() {
+  KMap m{};
+  int kk = 0;
+  for (int q = 0; q < NQ; ++q) {
+    const int len = G::tab.len[q];
+    const int padded = (len + 15) / 16 * 16;
+    for (int j = 0; j < padded; ++j, ++kk) {
+      if (j % 16 == 0) {
+        m.kq[kk / 16] = q;
+        m.first[kk / 16] = j == 0 ? 1 : 0;
+      }
+      if (j < len) {
+        const int l = G::tab.idx[q][j];
+        m.off[kk] = G::tab.off[l][0] + T::SX * (G::tab.off[l][1] + T::SY * G::tab.off[l][2]);
+      } else {
+        m.off[kk] = kPad;
+      }
+    }
+  }
+  return m;
+}
+static_assert(make_kmap().kq[KS - 1] == NQ - 1, "23 k-steps");
+__constant__ KMap c_kmap = make_kmap();
+
+// shared memory (bytes)
+struct TSmem {
+  static constexpr int b_off = 0;
+  static constexpr int a_off = B_BYTES;                          // ring of NB A buffers
+  static constexpr int tile_off = a_off + NB * A_BUF;            // (NV + 1) x SN floats
+  static constexpr int red_off = tile_off + (NV + 1) * SN * 4;   // [2][128] floats
+  static constexpr int beta_off = red_off + 2 * 128 * 4;         // [128][NQ] floats
+  static constexpr int pack_off = beta_off + 128 * NQ * 4;       // gate parameters
+  static constexpr int bar_off = (pack_off + (int)sizeof(gate::Pack<3>) + 15) / 16 * 16;
+  static constexpr int total = bar_off + 8 * (NB + 1) + 16;
+};
+static_assert(TSmem::total <= 232448, "shared memory of one CTA");
+static_assert(128 * gate::Dims<3>::LDX * 2 + 128 * 4 <= NB * A_BUF, "gate staging fits in the A ring");
+
+// byte offset of (row, k) in a K-major FP16 tile of 16 columns (core matrices 8 x 16 B)
+__host__ __device__ constexpr int tile_byte(int row, int k) {
+  return (row / 8) * 256 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2;
+}
+
+__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode, int ntiles,
+                                                             const double* __restrict__ U,
+                                                             const float* __restrict__ S, float* faces,
+                                                             const unsigned char* __restrict__ gate_mask,
+                                                             const gate::Pack<3>* __restrict__ gpack, float zthresh,
+                                                             const uint4* __restrict__ bimg) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* Bs = tsm + TSmem::b_off;
+  unsigned char* As = tsm + TSmem::a_off;
+  float* sm = reinterpret_cast<float*>(tsm + TSmem::tile_off);
+  float* sp = sm + NV * SN;
+  float* red = reinterpret_cast<float*>(tsm + TSmem::red_off);
+  float* bpart = reinterpret_cast<float*>(tsm + TSmem::beta_off);
+  const float* cs1 = reinterpret_cast<const float*>(Bs + B1_BYTES + B2_BYTES);
+  const float* cs2 = cs1 + NQ * 32;
+  uint64_t* chunk_free = reinterpret_cast<uint64_t*>(tsm + TSmem::bar_off);
+  uint64_t* pass_done = chunk_free + NB;
+  uint32_t* tbase_s = reinterpret_cast<uint32_t*>(pass_done + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = tid & 127, h = tid >> 7;
+  const float gm1 = a.gammaf - 1.0f;
+  const long long ncell_f = face_ncell(a);
+  const int tiles_x = (a.n[0] + T::TX - 1) / T::TX, tiles_y = (a.n[1] + T::TY - 1) / T::TY;
+
+  // ---- once per CTA: B image, gate parameters, barriers, TMEM ----
+  for (int i = tid; i < B_BYTES / 16; i += TCT) reinterpret_cast<uint4*>(Bs)[i] = __ldg(bimg + i);
+  gate::Pack<3>* P = reinterpret_cast<gate::Pack<3>*>(tsm + TSmem::pack_off);
+  if (mode == 2) gate::load_pack<3>(gpack, P);
+  if (tid == 0) {
+    for (int i = 0; i < NB; ++i) tc::mbar_init(chunk_free + i, 1);
+    tc::mbar_init(pass_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(tbase_s, 512);
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tbase_s;
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t id32 = tc::idesc_f16_f32(128, 32), id64 = tc::idesc_f16_f32(128, 64);
+  const uint32_t a_addr = tc::smem_addr(As), b_addr = tc::smem_addr(Bs);
+
+  uint32_t it = 0, pd_parity = 0;
+  bool ok = true;
+
+  // one k-step: every thread writes its 8 columns (hi, lo) of row r into ring buffer it % NB,
+  // thread 0 then issues the three MMAs into TMEM column d_col
+  auto kstep = [&](const float (&x)[8], uint32_t d_col, uint32_t idesc, uint32_t b_hi, uint32_t b_lo, uint32_t acc) {
+    const int buf = (int)(it % NB);
+    const uint32_t use = it / NB;
+    if (use > 0 && !tc::mbar_wait(chunk_free + buf, (use - 1) & 1u, WAIT_LIMIT)) ok = false;
+    unsigned char* base = As + buf * A_BUF;
+    uint4 hi, lo;
+    float rs[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) rs[e] = x[e] - __half2float(__float2half_rn(x[e]));
+    hi.x = pack_half2(x[0], x[1]);
+    hi.y = pack_half2(x[2], x[3]);
+    hi.z = pack_half2(x[4], x[5]);
+    hi.w = pack_half2(x[6], x[7]);
+    lo.x = pack_half2(rs[0], rs[1]);
+    lo.y = pack_half2(rs[2], rs[3]);
+    lo.z = pack_half2(rs[4], rs[5]);
+    lo.w = pack_half2(rs[6], rs[7]);
+    const int ob = tile_byte(r, 8 * h);
+    *reinterpret_cast<uint4*>(base + ob) = hi;
+    *reinterpret_cast<uint4*>(base + A_BUF / 2 + ob) = lo;
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t ab = a_addr + buf * A_BUF;
+      const uint64_t ahi = tc::smem_desc(ab, 128, 256), alo = tc::smem_desc(ab + A_BUF / 2, 128, 256);
+      const uint64_t bhi = tc::smem_desc(b_hi, 128, 256), blo = tc::smem_desc(b_lo, 128, 256);
+      tc::mma_f16(tbase + d_col, ahi, bhi, idesc, acc);
+      tc::mma_f16(tbase + d_col, ahi, blo, idesc, 1u);
+      tc::mma_f16(tbase + d_col, alo, bhi, idesc, 1u);
+      tc::commit(chunk_free + buf);
+    }
+    ++it;
+  };
+  auto finish_pass = [&]() {
+    if (tid == 0) tc::commit(pass_done);
+    if (!tc::mbar_wait(pass_done, pd_parity, WAIT_LIMIT)) ok = false;
+    pd_parity ^= 1u;
+    tc::fence_after_sync();
+  };
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int b = tile;
+    const int bx = b % tiles_x;
+    b /= tiles_x;
+    const int by = b % tiles_y;
+    const int bz = b / tiles_y;
+    __syncthreads();  // the previous tile's tail is done with the staged cells
+    stage_tile(a, S, sm, sp, bx * T::TX - T::H, by * T::TY - T::H, a.zf_first + bz * T::TZ - T::H, TCT);
+    __syncthreads();
+    // the cell of row r
+    const int lx = r % T::TX, ly = (r / T::TX) % T::TY, lz = r / (T::TX * T::TY);
+    const int x = bx * T::TX + lx, y = by * T::TY + ly, l = bz * T::TZ + lz;
+    const int z = l < a.zf_count ? slab_plane(a, l) : -1;
+    const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (lz + T::H));
+    const bool active = x < a.n[0] && y < a.n[1] && z >= 0;
+    const long long cell = active ? ((long long)z * a.n[1] + y) * a.n[0] + x : 0;
+    const long long fcell = active ? ((long long)l * a.n[1] + y) * a.n[0] + x : 0;
+
+    // which rows are linear (gated modes); the gate's staging lives in the A ring (free here:
+    // the previous tile's last pass has completed)
+    bool smooth = false;
+    if (mode == 2) {
+      using DM = gate::Dims<3>;
+      __nv_bfloat16* xs_all = reinterpret_cast<__nv_bfloat16*>(As);
+      float* zs = reinterpret_cast<float*>(As + 128 * DM::LDX * 2);
+      if (h == 0) {
+        float f[DM::NIN];
+        r32::gate_features_tile<3, 3>(sm, sp, c, f, std::make_integer_sequence<int, Geo<3, 2>::N0>{});
+        __nv_bfloat16* xs = xs_all + warp * 32 * DM::LDX;
+#pragma unroll
+        for (int k = 0; k < DM::KIN; ++k) xs[lane * DM::LDX + k] = __float2bfloat16_rn(k < DM::NIN ? f[k] : 0.0f);
+        __syncwarp();
+        float h1[2][4][4], h2[2][4][4], zf[2][4];
+        gate::forward32<3>(*P, xs, h1, h2, zf);
+        if ((lane & 3) == 0) {
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            zs[warp * 32 + 16 * mt + (lane >> 2)] = zf[mt][0];
+            zs[warp * 32 + 16 * mt + (lane >> 2) + 8] = zf[mt][2];
+          }
+        }
+      }
+      __syncthreads();
+      smooth = zs[r] > zthresh;
+      __syncthreads();  // the ring is written from here on
+    }
+    const bool weno_row = active && (mode == 0 || (mode == 2 && !smooth) || (mode == 3 && !gate_mask[cell]));
+    const bool weno_tile = __syncthreads_or(weno_row) != 0;
+
+#pragma unroll 1
+    for (int v = 0; v < NV && ok; ++v) {
+      const Ref ref(sm, c, v, gm1);
+      auto delta_at = [&](int kk) -> float {
+        const int o = c_kmap.off[kk];
+        return (active && o != kPad) ? ref.delta(sm, c + o) : 0.0f;
+      };
+      // s = power of two >= max |delta| over S0 (both halves of the row agree)
+      float mx = 0.0f;
+      for (int k = h; k < c_pairs.start[1]; k += 2) mx = fmaxf(mx, fabsf(ref.delta(sm, c + c_pairs.off[k])));
+      red[h * 128 + r] = active ? mx : 0.0f;
+      __syncthreads();
+      mx = fmaxf(red[r], red[128 + r]);
+      int ex = 0;
+      if (mx > 0.0f) frexpf(mx, &ex);
+      const float inv_s = ldexpf(1.0f, -ex), sc = ldexpf(1.0f, ex);
+
+      float coef[NQ];
+      coef[0] = 1.0f;
+#pragma unroll
+      for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
+      if (weno_tile) {
+        // ---- pass 1: derivative values of every stencil ----
+#pragma unroll 1
+        for (int j = 0; j < KS; ++j) {
+          float xv[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) xv[e] = delta_at(16 * j + 8 * h + e) * inv_s;
+          const int q = c_kmap.kq[j];
+          kstep(xv, 32u * q, id32, b_addr + j * B1_BLOCK, b_addr + j * B1_BLOCK + B1_BLOCK / 2,
+                c_kmap.first[j] ? 0u : 1u);
+        }
+        finish_pass();
+        // beta'_q = sum_m (D1 * column scale)^2 for this half's four stencils
+#pragma unroll 1
+        for (int qq = 0; qq < 4; ++qq) {
+          const int q = 4 * h + qq;
+          float d0[16], d1[16];
+          tc::tmem_ld16(tbase + lane_base + 32u * q, d0);
+          tc::tmem_ld16(tbase + lane_base + 32u * q + 16u, d1);
+          float bq = 0.0f;
+#pragma unroll
+          for (int m = 0; m < 16; ++m) {
+            const float dm = d0[m] * cs1[q * 32 + m];
+            bq = fmaf(dm, dm, bq);
+          }
+#pragma unroll
+          for (int m = 16; m < M; ++m) {
+            const float dm = d1[m - 16] * cs1[q * 32 + m];
+            bq = fmaf(dm, dm, bq);
+          }
+          bpart[r * NQ + q] = bq;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (weno_row) {
+          // nonlinear weights (Eq. 24, scaled form; the common factor 1/s^2 of beta' cancels in the
+          // ratios, eps/beta_max^2 uses the true beta_max = beta'_max s^2) and WENO-AO coefficients
+          float beta[NQ], bmax = 0.0f;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            beta[q] = bpart[r * NQ + q];
+            bmax = fmaxf(bmax, beta[q]);
+          }
+          if (bmax > 0.0f) {
+            const float ib = __frcp_rn(bmax);
+            const float is2 = inv_s * inv_s;
+            const float e = fmaxf(a.epsf * (ib * is2) * (ib * is2), 1e-30f);
+            float om[NQ], sum = 0.0f;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+              const float bq = beta[q] * ib;
+              om[q] = __fdividef((float)linear_weight<3>(q), fmaf(bq, bq, e));
+              sum += om[q];
+            }
+            const float inv = __frcp_rn(sum);
+            const float w0 = om[0] * inv;
+            coef[0] = w0 / (float)linear_weight<3>(0);
+#pragma unroll
+            for (int q = 1; q < NQ; ++q)
+              coef[q] = fmaf(-w0, (float)(linear_weight<3>(q) / linear_weight<3>(0)), om[q] * inv);
+          }
+        }
+      }
+      // ---- pass 2: blended face values (S0 only on an all-linear tile) ----
+      const int ks_end = weno_tile ? KS : 8;
+#pragma unroll 1
+      for (int j = 0; j < ks_end; ++j) {
+        const int q = c_kmap.kq[j];
+        float cq = coef[0];
+#pragma unroll
+        for (int qq = 1; qq < NQ; ++qq) cq = (q == qq) ? coef[qq] : cq;
+        const float f = cq * inv_s;
+        float xv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) xv[e] = delta_at(16 * j + 8 * h + e) * f;
+        kstep(xv, 256u, id64, b_addr + B1_BYTES + j * B2_BLOCK, b_addr + B1_BYTES + j * B2_BLOCK + B2_BLOCK / 2,
+              j == 0 ? 0u : 1u);
+      }
+      finish_pass();
+      {
+        float d0[16], d1[16];
+        tc::tmem_ld16(tbase + lane_base + 256u + 32u * h, d0);
+        tc::tmem_ld16(tbase + lane_base + 256u + 32u * h + 16u, d1);
+        if (active) {
+#pragma unroll
+          for (int m = 0; m < 32; ++m) {
+            const int sp_ = 32 * h + m;
+            if (sp_ < F) *slot(faces, ncell_f, fcell, sp_, v) = (m < 16 ? d0[m] : d1[m - 16]) * cs2[sp_] * sc;
+          }
+        }
+      }
+      tc::fence_before_sync();
+      ok = __syncthreads_and(ok) != 0;
+    }
+    if (!ok) break;
+    __syncthreads();  // every dW slot of the tile written
+    if (h == 0 && active)
+      r32::write_states<3, 3>(a, sm, sp, c, U, (long long)a.n[0] * a.n[1] * a.n[2], cell, fcell, ncell_f, faces,
+                              [&](int s_, int v_) { return *slot(faces, ncell_f, fcell, s_, v_); });
+  }
+  if (!ok) {
+    if (tid == 0) raise_flag(a.status, kFlagTimeout);
+    // let whatever is still in flight finish (bounded) before the TMEM goes back
+    if (tid == 0) tc::commit(pass_done);
+    tc::mbar_wait(pass_done, pd_parity, WAIT_LIMIT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+}  // namespace tcg
 }  // namespace r33
 
 size_t recon33_table_floats() { return (size_t)r33::NP * r33::ROW; }
@@ -365,9 +737,98 @@ void recon33_fill_table(const double* w, float* out) {
   }
 }
 
+size_t recon33_tc_image_bytes() { return (size_t)r33::tcg::B_BYTES; }
+
+// FP16 hi/lo image of the weights in the tensor-core kernel's shared-memory layout: pass-1 blocks
+// (per k-step: 32 derivative columns of its stencil x 16 K, hi then lo), pass-2 blocks (64 face
+// columns x 16 K), then the power-of-two column scales (pass 1 per stencil, pass 2)
+void recon33_tc_fill_image(const double* w, unsigned char* out) {
+  using namespace r33;
+  using namespace r33::tcg;
+  constexpr StencilTable tab = make_stencil(3, 3);
+  constexpr KMap km = make_kmap();
+  int woffq[NQ], kstart[NQ];
+  for (int q = 0, wo = 0, ks = 0; q < NQ; ++q) {
+    woffq[q] = wo;
+    kstart[q] = ks;
+    wo += tab.len[q] * (F + M);
+    ks += (tab.len[q] + 15) / 16 * 16;
+  }
+  // weight of output column n (pass 1: derivative n of stencil q; pass 2: face point n) at padded K kk
+  auto weight = [&](int pass, int n, int kk) -> double {
+    const int q = km.kq[kk / 16];
+    const int jin = kk - kstart[q], len = tab.len[q];
+    if (jin >= len) return 0.0;
+    if (pass == 1) return n < M ? w[woffq[q] + F * len + n * len + jin] : 0.0;
+    return n < F ? w[woffq[q] + n * len + jin] : 0.0;
+  };
+  float* cs = reinterpret_cast<float*>(out + B1_BYTES + B2_BYTES);
+  float scale1[NQ][32], scale2[64];
+  for (int q = 0; q < NQ; ++q)
+    for (int n = 0; n < 32; ++n) {
+      double mx = 0.0;
+      for (int kk = 0; kk < KT; ++kk)
+        if (km.kq[kk / 16] == q) mx = std::fmax(mx, std::fabs(weight(1, n, kk)));
+      int e = 0;
+      if (mx > 0.0) std::frexp(mx, &e);
+      scale1[q][n] = (float)std::ldexp(1.0, -e);
+      cs[q * 32 + n] = (float)std::ldexp(1.0, e);
+    }
+  for (int n = 0; n < 64; ++n) {
+    double mx = 0.0;
+    for (int kk = 0; kk < KT; ++kk) mx = std::fmax(mx, std::fabs(weight(2, n, kk)));
+    int e = 0;
+    if (mx > 0.0) std::frexp(mx, &e);
+    scale2[n] = (float)std::ldexp(1.0, -e);
+    cs[NQ * 32 + n] = (float)std::ldexp(1.0, e);
+  }
+  auto put = [&](unsigned char* blk, int rows, int n, int k, float v) {
+    const __half hi = __float2half_rn(v);
+    const __half lo = __float2half_rn(v - __half2float(hi));
+    *reinterpret_cast<__half*>(blk + tile_byte(n, k)) = hi;
+    *reinterpret_cast<__half*>(blk + rows * 32 + tile_byte(n, k)) = lo;
+  };
+  for (int j = 0; j < KS; ++j) {
+    const int q = km.kq[j];
+    unsigned char* b1 = out + j * B1_BLOCK;
+    unsigned char* b2 = out + B1_BYTES + j * B2_BLOCK;
+    for (int k = 0; k < 16; ++k) {
+      for (int n = 0; n < 32; ++n) put(b1, 32, n, k, (float)(weight(1, n, 16 * j + k) * scale1[q][n]));
+      for (int n = 0; n < 64; ++n) put(b2, 64, n, k, (float)(weight(2, n, 16 * j + k) * scale2[n]));
+    }
+  }
+}
+
+cudaError_t launch_recon32_33_tc(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st,
+                                 int zf_first, int zf_count) {
+  using namespace r33;
+  GridArgs a = make_grid_args(ctx);
+  if (zf_count > 0) {
+    a.zf_first = zf_first;
+    a.zf_count = zf_count;
+  }
+  const int ntiles = ((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
+                     ((a.zf_count + T::TZ - 1) / T::TZ);
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tcg::recon33_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::TSmem::total);
+  if (e != cudaSuccess) return e;
+  const int grid = ntiles < nsm ? ntiles : nsm;
+  const float th = (float)ctx->gate_threshold;
+  const float zth = logf(th / (1.0f - th));
+  tcg::recon33_tc_kernel<<<grid, tcg::TCT, tcg::TSmem::total, st>>>(
+      a, ctx->recon, ntiles, U, shadow, faces, ctx->d_gate_mask, (const gate::Pack<3>*)ctx->d_gate_pack, zth,
+      reinterpret_cast<const uint4*>(ctx->d_w33tc));
+  ctx->launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_recon32_33(kfvm_ctx* ctx, const double* U, const float* shadow, float* faces, cudaStream_t st,
                               int zf_first, int zf_count) {
   using namespace r33;
+  if (ctx->tensor_cores && ctx->d_w33tc) return launch_recon32_33_tc(ctx, U, shadow, faces, st, zf_first, zf_count);
   GridArgs a = make_grid_args(ctx);
   if (zf_count > 0) {
     a.zf_first = zf_first;
