@@ -45,11 +45,13 @@ struct T32 {
   static constexpr int SN = SX * SY * SZ;
   static constexpr int THREADS = TX * TY * TZ;
 };
-// d = 3, R = 3: an 8 x 4 x 4 tile keeps the radius-3 halo at 1400 cells
+// d = 3, R = 3: an 8 x 4 x 4 tile keeps the radius-3 halo at 1400 cells; the planes are padded
+// from 14 x 10 to 14 x 12 = 168 cells (= 8 mod 32 banks), so that 32 cells of one y row and
+// four z planes read 32 different banks at any common stencil offset
 template <>
 struct T32<3, 3> {
   static constexpr int TX = 8, TY = 4, TZ = 4, H = 3;
-  static constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SZ = TZ + 2 * H;
+  static constexpr int SX = TX + 2 * H, SY = TY + 2 * H + 2, SZ = TZ + 2 * H;
   static constexpr int SN = SX * SY * SZ;
   static constexpr int THREADS = TX * TY * TZ;
 };

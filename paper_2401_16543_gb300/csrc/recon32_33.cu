@@ -369,16 +369,20 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
 //           D2 of 64 columns (54 used).
 // Tiles whose cells are all linear (gated modes) skip pass 1 and run the 8 k-steps
 // of S0 only.  The CTA is persistent (one per SM): B (138 KB, FP16 hi/lo) is
-// loaded into shared memory once; 256 threads build A chunks (cell r = t % 128,
-// half h = t / 128 of each 16-wide k-step) in a ring of 4 buffers, thread 0 issues
-// the MMAs and commits each buffer back to its mbarrier.  Every wait has an
-// iteration limit; on expiry the kernel raises the timeout flag and stops.
+// loaded into shared memory once; 512 threads build A chunks (cell r = t % 128,
+// quarter h = t / 128 of each 16-wide k-step) in a ring of 4 buffers, thread 0
+// issues the MMAs and commits each buffer back to its mbarrier (a hand-off through
+// per-buffer "full" mbarriers instead of the CTA barrier measured 10% slower).  The scale s of a
+// (cell, variable) is the power of two at or above the central cell's own scale
+// (rho~, sound speed, p~), so A stays O(1) (FP16 range and subnormals cost at most
+// ~3e-8 of that scale).  Every wait has an iteration limit; on expiry the kernel
+// raises the timeout flag and stops.
 // ===========================================================================
 namespace tcg {
 
 constexpr int KS = 23;                     // k-steps of 16
 constexpr int KT = KS * 16;                // padded K = 368
-constexpr int TCT = 256;                   // threads per CTA
+constexpr int TCT = 512;                   // threads per CTA: 4 per cell row (a quarter of each k-step)
 constexpr int NB = 4;                      // A ring buffers
 constexpr int B1_BLOCK = 2048;             // pass-1 B block: 32 x 16 FP16, hi + lo
 constexpr int B2_BLOCK = 4096;             // pass-2 B block: 64 x 16 FP16, hi + lo
@@ -425,8 +429,7 @@ struct TSmem {
   static constexpr int b_off = 0;
   static constexpr int a_off = B_BYTES;                          // ring of NB A buffers
   static constexpr int tile_off = a_off + NB * A_BUF;            // (NV + 1) x SN floats
-  static constexpr int red_off = tile_off + (NV + 1) * SN * 4;   // [2][128] floats
-  static constexpr int beta_off = red_off + 2 * 128 * 4;         // [128][NQ] floats
+  static constexpr int beta_off = tile_off + (NV + 1) * SN * 4;  // [128][NQ] floats
   static constexpr int pack_off = beta_off + 128 * NQ * 4;       // gate parameters
   static constexpr int bar_off = (pack_off + (int)sizeof(gate::Pack<3>) + 15) / 16 * 16;
   static constexpr int total = bar_off + 8 * (NB + 1) + 16;
@@ -455,7 +458,6 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   unsigned char* As = tsm + TSmem::a_off;
   float* sm = reinterpret_cast<float*>(tsm + TSmem::tile_off);
   float* sp = sm + NV * SN;
-  float* red = reinterpret_cast<float*>(tsm + TSmem::red_off);
   float* bpart = reinterpret_cast<float*>(tsm + TSmem::beta_off);
   const float* cs1 = reinterpret_cast<const float*>(Bs + B1_BYTES + B2_BYTES);
   const float* cs2 = cs1 + NQ * 32;
@@ -493,26 +495,22 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
 
   // one k-step: every thread writes its 8 columns (hi, lo) of row r into ring buffer it % NB,
   // thread 0 then issues the three MMAs into TMEM column d_col
-  auto kstep = [&](const float (&x)[8], uint32_t d_col, uint32_t idesc, uint32_t b_hi, uint32_t b_lo, uint32_t acc) {
+  auto kstep = [&](const float (&x)[4], uint32_t d_col, uint32_t idesc, uint32_t b_hi, uint32_t b_lo, uint32_t acc) {
     const int buf = (int)(it % NB);
     const uint32_t use = it / NB;
     if (use > 0 && !tc::mbar_wait(chunk_free + buf, (use - 1) & 1u, WAIT_LIMIT)) ok = false;
     unsigned char* base = As + buf * A_BUF;
-    uint4 hi, lo;
-    float rs[8];
+    uint2 hi, lo;
+    float rs[4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) rs[e] = x[e] - __half2float(__float2half_rn(x[e]));
+    for (int e = 0; e < 4; ++e) rs[e] = x[e] - __half2float(__float2half_rn(x[e]));
     hi.x = pack_half2(x[0], x[1]);
     hi.y = pack_half2(x[2], x[3]);
-    hi.z = pack_half2(x[4], x[5]);
-    hi.w = pack_half2(x[6], x[7]);
     lo.x = pack_half2(rs[0], rs[1]);
     lo.y = pack_half2(rs[2], rs[3]);
-    lo.z = pack_half2(rs[4], rs[5]);
-    lo.w = pack_half2(rs[6], rs[7]);
-    const int ob = tile_byte(r, 8 * h);
-    *reinterpret_cast<uint4*>(base + ob) = hi;
-    *reinterpret_cast<uint4*>(base + A_BUF / 2 + ob) = lo;
+    const int ob = tile_byte(r, 4 * h);
+    *reinterpret_cast<uint2*>(base + ob) = hi;
+    *reinterpret_cast<uint2*>(base + A_BUF / 2 + ob) = lo;
     tc::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
@@ -543,8 +541,9 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
     __syncthreads();  // the previous tile's tail is done with the staged cells
     stage_tile(a, S, sm, sp, bx * T::TX - T::H, by * T::TY - T::H, a.zf_first + bz * T::TZ - T::H, TCT);
     __syncthreads();
-    // the cell of row r
-    const int lx = r % T::TX, ly = (r / T::TX) % T::TY, lz = r / (T::TX * T::TY);
+    // the cell of row r: a warp holds one y row of the tile across its four z planes (conflict-free
+    // shared-memory gathers, see T32<3, 3>)
+    const int lx = r % T::TX, lz = (r / T::TX) % T::TZ, ly = r / (T::TX * T::TZ);
     const int x = bx * T::TX + lx, y = by * T::TY + ly, l = bz * T::TZ + lz;
     const int z = l < a.zf_count ? slab_plane(a, l) : -1;
     const int c = (lx + T::H) + T::SX * ((ly + T::H) + T::SY * (lz + T::H));
@@ -590,14 +589,11 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
         const int o = c_kmap.off[kk];
         return (active && o != kPad) ? ref.delta(sm, c + o) : 0.0f;
       };
-      // s = power of two >= max |delta| over S0 (both halves of the row agree)
-      float mx = 0.0f;
-      for (int k = h; k < c_pairs.start[1]; k += 2) mx = fmaxf(mx, fabsf(ref.delta(sm, c + c_pairs.off[k])));
-      red[h * 128 + r] = active ? mx : 0.0f;
-      __syncthreads();
-      mx = fmaxf(red[r], red[128 + r]);
+      // s = power of two at or above the central cell's scale of this variable
+      const float pc = sp[c];
+      const float scale = v == 0 ? ref.uc[0] : (v == NV - 1 ? pc : sqrtf(fmaxf(a.gammaf * pc * ref.irt, 0.0f)));
       int ex = 0;
-      if (mx > 0.0f) frexpf(mx, &ex);
+      if (scale > 0.0f && scale < 3.0e38f) frexpf(scale, &ex);
       const float inv_s = ldexpf(1.0f, -ex), sc = ldexpf(1.0f, ex);
 
       float coef[NQ];
@@ -608,18 +604,18 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
         // ---- pass 1: derivative values of every stencil ----
 #pragma unroll 1
         for (int j = 0; j < KS; ++j) {
-          float xv[8];
+          float xv[4];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) xv[e] = delta_at(16 * j + 8 * h + e) * inv_s;
+          for (int e = 0; e < 4; ++e) xv[e] = delta_at(16 * j + 4 * h + e) * inv_s;
           const int q = c_kmap.kq[j];
           kstep(xv, 32u * q, id32, b_addr + j * B1_BLOCK, b_addr + j * B1_BLOCK + B1_BLOCK / 2,
                 c_kmap.first[j] ? 0u : 1u);
         }
         finish_pass();
-        // beta'_q = sum_m (D1 * column scale)^2 for this half's four stencils
+        // beta'_q = sum_m (D1 * column scale)^2 for this quarter's two stencils
 #pragma unroll 1
-        for (int qq = 0; qq < 4; ++qq) {
-          const int q = 4 * h + qq;
+        for (int qq = 0; qq < 2; ++qq) {
+          const int q = 2 * h + qq;
           float d0[16], d1[16];
           tc::tmem_ld16(tbase + lane_base + 32u * q, d0);
           tc::tmem_ld16(tbase + lane_base + 32u * q + 16u, d1);
@@ -676,22 +672,21 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
 #pragma unroll
         for (int qq = 1; qq < NQ; ++qq) cq = (q == qq) ? coef[qq] : cq;
         const float f = cq * inv_s;
-        float xv[8];
+        float xv[4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) xv[e] = delta_at(16 * j + 8 * h + e) * f;
+        for (int e = 0; e < 4; ++e) xv[e] = delta_at(16 * j + 4 * h + e) * f;
         kstep(xv, 256u, id64, b_addr + B1_BYTES + j * B2_BLOCK, b_addr + B1_BYTES + j * B2_BLOCK + B2_BLOCK / 2,
               j == 0 ? 0u : 1u);
       }
       finish_pass();
       {
-        float d0[16], d1[16];
-        tc::tmem_ld16(tbase + lane_base + 256u + 32u * h, d0);
-        tc::tmem_ld16(tbase + lane_base + 256u + 32u * h + 16u, d1);
+        float d0[16];
+        tc::tmem_ld16(tbase + lane_base + 256u + 16u * h, d0);
         if (active) {
 #pragma unroll
-          for (int m = 0; m < 32; ++m) {
-            const int sp_ = 32 * h + m;
-            if (sp_ < F) *slot(faces, ncell_f, fcell, sp_, v) = (m < 16 ? d0[m] : d1[m - 16]) * cs2[sp_] * sc;
+          for (int m = 0; m < 16; ++m) {
+            const int sp_ = 16 * h + m;
+            if (sp_ < F) *slot(faces, ncell_f, fcell, sp_, v) = d0[m] * cs2[sp_] * sc;
           }
         }
       }
