@@ -119,7 +119,16 @@ size_t kfvm_weights_count(const kfvm_ctx* ctx);
  *                 Sec. 4 to the Riemann states; 0 off.
  *   "kappa", "eta"  bound relaxation and flattener of Sec. 4.1 (0.1, 0).
  *   "eps"         epsilon of the nonlinear weights, Eq. 24 (1e-40).
+ *                 (3 is set by kfvm_set_smooth_mask: gated by a caller mask.)
  *   "gate_threshold"  probability above which a cell is treated as smooth (0.5).
+ *   "tensor_cores" 1 (default) / 0: in the FP32 mode with dims = 3, radius 3,
+ *                 run the stencil contraction on the tcgen05 tensor cores (FP16
+ *                 hi/lo split operands, FP32 accumulation in tensor memory) or
+ *                 on the FP32 pipe.  Ignored elsewhere.
+ *   "slab_planes" 3D only: process kfvm_step / kfvm_rhs in z-slabs of this many
+ *                 planes (at most what the Riemann-state buffer was sized for;
+ *                 kfvm_init sizes it to the whole grid up to 8 GiB, else to
+ *                 slabs).  Results do not depend on the slab size.
  *   "profile"     1: time every hot-path launch with CUDA events (see
  *                 kfvm_profile_get); 0 (default) off.
  * Errors: KFVM_ERR_ARG for an unknown key or value out of range. */
