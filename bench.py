@@ -77,6 +77,12 @@ def _workloads():
             "2D Euler 2048x2048, radius 2, learned gate: 256 seeded Voronoi regions (seed 4), each smooth sine or a "
             "constant (coin 1/2), outflow, SSP-RK3 at CFL 0.4",
             lambda dev: wl.mixed_voronoi(2, 2048, 256, seed=4, device=dev), gate="gate_params_2d.npy", cpu_crop=128),
+        "mixed3d-64-r3": Workload(
+            "mixed3d-64-r3", 3, 3, [64, 64, 64], "outflow",
+            "3D Euler 64^3, radius 3, learned gate + mixed precision: 8 seeded Voronoi regions (seed 5), each "
+            "smooth sine or a constant, outflow, SSP-RK3 at CFL 0.4 (the 512^3 workload's scheme on a grid that "
+            "profilers can capture)",
+            lambda dev: wl.mixed_voronoi(3, 64, 8, seed=5, R=3, device=dev), gate="gate_params_3d.npy", cpu_crop=16),
         "mixed3d-512-r3": Workload(
             "mixed3d-512-r3", 3, 3, [512, 512, 512], "outflow",
             "3D Euler 512^3, radius 3, learned gate + mixed precision: 512 seeded Voronoi regions (seed 5), each smooth "
@@ -100,7 +106,7 @@ def parse():
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline path only (no other paths, e2e or CPU baseline): for profiler runs")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=["voronoi2d-1024", "halfsine3d-256", "mixed2d-2048", "mixed3d-512-r3"])
+                    choices=["voronoi2d-1024", "halfsine3d-256", "mixed2d-2048", "mixed3d-64-r3", "mixed3d-512-r3"])
     return ap.parse_args()
 
 
