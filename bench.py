@@ -244,10 +244,25 @@ def make_solver(W, path, n=None):
     return g
 
 
-def measure_path(W, path, U0, steps, warmup, stream, flush_buf, n=None, min_warm_s=0.0):
+def job_time_ms(ms, dist, device):
+    """The job's time: the maximum over ranks (every rank runs its own replica of the workload)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, ncell, steps, ms):
+    """Whole-job cell-updates/s per RK stage: every rank's cells x 3 stages x steps over the job time."""
+    return world * ncell * 3 * steps / (ms * 1e-3)
+
+
+def measure_path(W, path, U0, steps, warmup, stream, flush_buf, n=None, min_warm_s=0.0, barrier=None):
     """W warm-up steps (and, with min_warm_s, at least that many seconds of steps, so that the clock
     sampler is running and the GPU is at its loaded clocks when the timed steps start), then the
-    timed steps from the initial state."""
+    timed steps from the initial state, bracketed by `barrier` (all ranks) and a device sync."""
     import torch
     g = make_solver(W, path, n)
     U = U0.clone()
@@ -269,8 +284,13 @@ def measure_path(W, path, U0, steps, warmup, stream, flush_buf, n=None, min_warm
         launches0 = g.launches
         g.set_option("profile", 1)
         g.profile_reset()
+        if barrier is not None:
+            barrier()
+        torch.cuda.synchronize()
         ms = time_steps(g, U, steps, stream, flush_buf)
         torch.cuda.synchronize()
+        if barrier is not None:
+            barrier()
         prof = g.profile()
         g.set_option("profile", 0)
         launches = g.launches - launches0
@@ -309,19 +329,12 @@ def main():
     sampler = ClockSampler(torch.cuda.current_device() if world == 1 else local)
     sampler.start()
     # ---- headline path, resident inputs ----
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
+    barrier = dist.barrier if dist is not None else None
     g, ms, prof, launches, g_final_state = measure_path(W, path, U0, args.steps, args.warmup, stream, flush_buf,
-                                                        min_warm_s=1.0)
-    torch.cuda.synchronize()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+                                                        min_warm_s=1.0, barrier=barrier)
+    ms = job_time_ms(ms, dist, dev)
     clocks = sampler.stop()
-    value = world * ncell * 3 * args.steps / (ms * 1e-3)
+    value = job_value(world, ncell, args.steps, ms)
     print(f"[bench] {path}: {ms / args.steps:.3f} ms per step", file=sys.stderr, flush=True)
 
     # ---- the other paths on the same workload (plain FP64 is the metric's reference) ----
@@ -337,9 +350,11 @@ def main():
             n_o = W.n[:2] + [W.fp64_planes]
             note = f"first {W.fp64_planes} z-planes of the state ({W.n[0]}x{W.n[1]}x{W.fp64_planes} cells)"
             k = 1
-        _, mso, _, _, _ = measure_path(W, other, Uo0, k, 1 if other == "fp64" else 2, stream, flush_buf, n_o)
+        _, mso, _, _, _ = measure_path(W, other, Uo0, k, 1 if other == "fp64" else 2, stream, flush_buf, n_o,
+                                       barrier=barrier)
+        mso = job_time_ms(mso, dist, dev)
         cells = ncell if n_o is None else n_o[0] * n_o[1] * n_o[2]
-        others[other] = {"value": world * cells * 3 * k / (mso * 1e-3), "ms_per_step": mso / k, "steps": k}
+        others[other] = {"value": job_value(world, cells, k, mso), "ms_per_step": mso / k, "steps": k}
         print(f"[bench] {other}: {mso / k:.3f} ms per step", file=sys.stderr, flush=True)
         if note:
             others[other]["sample"] = note
@@ -377,7 +392,8 @@ def main():
         e1.synchronize()
         ms_e2e = e0.elapsed_time(e1)
     g.sync_status(stream)
-    e2e = {"value": world * ncell * 3 * args.steps / (ms_e2e * 1e-3), "unit": "cell-updates/s",
+    ms_e2e = job_time_ms(ms_e2e, dist, dev)
+    e2e = {"value": job_value(world, ncell, args.steps, ms_e2e), "unit": "cell-updates/s",
            "h2d_bytes_per_step": Uh.numel() * 8, "d2h_bytes_per_step": Uo.numel() * 8}
 
     # ---- roofline of the dominant kernel ----

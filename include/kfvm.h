@@ -129,6 +129,11 @@ size_t kfvm_weights_count(const kfvm_ctx* ctx);
  *                 planes (at most what the Riemann-state buffer was sized for;
  *                 kfvm_init sizes it to the whole grid up to 8 GiB, else to
  *                 slabs).  Results do not depend on the slab size.
+ *   "timeout_probe" 1: test hook of the bounded device waits: the next
+ *                 tensor-core launch waits on a barrier phase nothing completes,
+ *                 gives up after a short limit, raises the timeout flag (read by
+ *                 kfvm_sync_status as KFVM_ERR_TIMEOUT) and does no work; the
+ *                 option resets itself and the context stays usable.
  *   "profile"     1: time every hot-path launch with CUDA events (see
  *                 kfvm_profile_get); 0 (default) off.
  * Errors: KFVM_ERR_ARG for an unknown key or value out of range. */

@@ -415,6 +415,9 @@ kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double v) {
   } else if (k == "tensor_cores") {
     if (v != 0 && v != 1) return KFVM_ERR_ARG;
     ctx->tensor_cores = (int)v;
+  } else if (k == "timeout_probe") {
+    if (v != 0 && v != 1) return KFVM_ERR_ARG;
+    ctx->timeout_probe = (int)v;
   } else if (k == "slab_planes") {
     // split 3D steps into z-slabs of this many planes (at most what the buffer was sized for)
     if (!(v >= 1) || ctx->dims != 3) return KFVM_ERR_ARG;

@@ -53,6 +53,7 @@ struct kfvm_ctx {
   // options
   int precision = 64, recon = 0, riemann = 0, positivity = 1;
   int tensor_cores = 1;  // d = 3, R = 3 FP32 contraction on tcgen05 (0: the CUDA-core kernel)
+  int timeout_probe = 0;  // test hook: the next tensor-core launch waits on nothing and times out
   double kappa = 0.1, eta = 0.0, eps = 1e-40, gate_threshold = 0.5;
   // weights
   size_t wcount = 0;

@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
                                                              const float* __restrict__ S, float* faces,
                                                              const unsigned char* __restrict__ gate_mask,
                                                              const gate::Pack<3>* __restrict__ gpack, float zthresh,
-                                                             const uint4* __restrict__ bimg) {
+                                                             const uint4* __restrict__ bimg, int timeout_probe) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char* Bs = tsm + TSmem::b_off;
   unsigned char* As = tsm + TSmem::a_off;
@@ -547,7 +547,14 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
     tc::fence_after_sync();
   };
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  // test hook of the bounded waits: wait on a phase that nothing completes (an mbarrier no thread
+  // arrives on), give up after a short limit, raise the timeout flag and do no work
+  if (timeout_probe) {
+    bool got = true;
+    if (tid == 0) got = tc::mbar_wait(pass_done, pd_parity, 1 << 10);  // phase 0 of a fresh barrier
+    ok = __syncthreads_and(got) != 0;
+  }
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     int b = tile;
     const int bx = b % tiles_x;
     b /= tiles_x;
@@ -837,7 +844,8 @@ cudaError_t launch_recon32_33_tc(kfvm_ctx* ctx, const double* U, const float* sh
   const float zth = logf(th / (1.0f - th));
   tcg::recon33_tc_kernel<<<grid, tcg::TCT, tcg::TSmem::total, st>>>(
       a, ctx->recon, ntiles, U, shadow, faces, ctx->d_gate_mask, (const gate::Pack<3>*)ctx->d_gate_pack, zth,
-      reinterpret_cast<const uint4*>(ctx->d_w33tc));
+      reinterpret_cast<const uint4*>(ctx->d_w33tc), ctx->timeout_probe);
+  ctx->timeout_probe = 0;
   ctx->launches += 1;
   return cudaGetLastError();
 }

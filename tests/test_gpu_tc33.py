@@ -106,3 +106,22 @@ def test_tc_all_linear_tiles_take_the_short_path(kfvm):
     h = _solver(kfvm, n, "outflow", 1, 1)
     f_lin = h.reconstruct(U0).cpu().numpy()
     assert np.array_equal(f_mask, f_lin)
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_survives(kfvm):
+    """The tensor-core kernel's waits have iteration limits: the test hook makes one wait on a phase
+    that nothing completes, the kernel raises the timeout flag instead of hanging, the host reads
+    KFVM_ERR_TIMEOUT, and the next reconstruction is correct."""
+    n = (10, 9, 6)
+    U0 = _state(n, seed=41).cuda()
+    g = _solver(kfvm, n, "outflow", 1)
+    ref = g.faces_primitive(g.reconstruct(U0)).cpu().numpy()
+    g.sync_status()
+    g.set_option("timeout_probe", 1)
+    g.reconstruct(U0)
+    with pytest.raises(kfvm.KfvmError) as e:
+        g.sync_status()
+    assert e.value.code == 6  # KFVM_ERR_TIMEOUT
+    again = g.faces_primitive(g.reconstruct(U0)).cpu().numpy()
+    g.sync_status()
+    assert np.array_equal(again, ref)
