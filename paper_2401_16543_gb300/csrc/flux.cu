@@ -420,7 +420,7 @@ struct FTile {
 };
 
 template <int D, int R, typename Real, bool SHADOW>
-__global__ void __launch_bounds__(FTile<D>::THREADS) flux_update_kernel(GridArgs a, const Real* __restrict__ faces,
+__global__ void __launch_bounds__(FTile<D>::THREADS, 5) flux_update_kernel(GridArgs a, const Real* __restrict__ faces,
                                                                         int stage, const double* __restrict__ U0,
                                                                         const double* __restrict__ Us,
                                                                         double* __restrict__ out,
