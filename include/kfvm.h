@@ -256,6 +256,19 @@ kfvm_status kfvm_gate_forward(kfvm_ctx* ctx, const float* X, float* prob, size_t
 kfvm_status kfvm_gate_train_step(kfvm_ctx* ctx, const float* X, const float* y, size_t n, float lr,
                                  float* loss_dev, float* grads_out, void* stream);
 
+/* Load the network from host memory: the packed parameters of
+ * kfvm_gate_set_params as float32 (bytes = 4 * kfvm_gate_param_count) or as
+ * bfloat16 (bytes = 2 * count, widened exactly to the float32 masters).
+ * Errors: KFVM_ERR_ARG for any other size. */
+kfvm_status kfvm_gate_load(kfvm_ctx* ctx, const void* host_weights, size_t bytes);
+
+/* `epochs` passes of Adam steps (kfvm_gate_train_step) over the n samples
+ * (X: device float32 [n][in], y: device float32 [n]) in consecutive
+ * mini-batches of 2048, in order (shuffle X, y beforehand if wanted).
+ * Errors: KFVM_ERR_ARG, KFVM_ERR_STATE (no network loaded), KFVM_ERR_CUDA. */
+kfvm_status kfvm_gate_train(kfvm_ctx* ctx, const float* X, const float* y, size_t n, int epochs, float lr,
+                            void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Introspection and lifetime                                                  */
 /* ------------------------------------------------------------------------- */

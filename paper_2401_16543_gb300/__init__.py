@@ -68,6 +68,8 @@ def load():
     L.kfvm_set_smooth_mask.argtypes = [P, P, P]
     L.kfvm_gate_mask.argtypes = [P, P, P, P]
     L.kfvm_gate_train_step.argtypes = [P, P, P, S, ctypes.c_float, P, P, P]
+    L.kfvm_gate_load.argtypes = [P, P, S]
+    L.kfvm_gate_train.argtypes = [P, P, P, S, I, ctypes.c_float, P]
     L.kfvm_stencil_info.argtypes = [I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
     L.kfvm_launch_count.argtypes = [P]
     L.kfvm_launch_count.restype = ctypes.c_longlong
@@ -275,6 +277,16 @@ class KFVM:
         p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
         _check(self._L.kfvm_gate_set_params(self._ctx, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size),
                "kfvm_gate_set_params")
+
+    def gate_load(self, weights):
+        """Load float32 or bfloat16 (numpy uint16 bit patterns) packed parameters."""
+        w = np.ascontiguousarray(weights)
+        _check(self._L.kfvm_gate_load(self._ctx, w.ctypes.data_as(ctypes.c_void_p), w.nbytes), "kfvm_gate_load")
+
+    def gate_train(self, X, y, epochs: int, lr: float, stream=None):
+        """Adam epochs over (X, y) in mini-batches of 2048 (device tensors)."""
+        _check(self._L.kfvm_gate_train(self._ctx, _ptr(X), _ptr(y), X.shape[0], int(epochs), float(lr),
+                                       _stream(stream)), "kfvm_gate_train")
 
     def gate_get_params(self) -> np.ndarray:
         p = np.zeros(self.gate_param_count, dtype=np.float32)

@@ -23,6 +23,7 @@
 #include <cstdint>
 #include <cstring>
 #include <utility>
+#include <vector>
 
 #include "gate.cuh"
 
@@ -543,6 +544,37 @@ kfvm_status kfvm_gate_train_step(kfvm_ctx* ctx, const float* X, const float* y, 
   return launch_gate_train(ctx, X, y, n, lr, loss_dev, grads_out, (cudaStream_t)stream) == cudaSuccess
              ? KFVM_OK
              : KFVM_ERR_CUDA;
+}
+
+kfvm_status kfvm_gate_load(kfvm_ctx* ctx, const void* host_weights, size_t bytes) {
+  if (!ctx || !host_weights) return KFVM_ERR_ARG;
+  const size_t count = kfvm_gate_param_count(ctx);
+  if (bytes == 4 * count) return kfvm_gate_set_params(ctx, static_cast<const float*>(host_weights), count);
+  if (bytes != 2 * count) return KFVM_ERR_ARG;
+  // bfloat16 parameters: widen to the float32 masters (exact)
+  std::vector<float> w(count);
+  const uint16_t* b = static_cast<const uint16_t*>(host_weights);
+  for (size_t i = 0; i < count; ++i) {
+    const uint32_t bits = (uint32_t)b[i] << 16;
+    std::memcpy(&w[i], &bits, 4);
+  }
+  return kfvm_gate_set_params(ctx, w.data(), count);
+}
+
+kfvm_status kfvm_gate_train(kfvm_ctx* ctx, const float* X, const float* y, size_t n, int epochs, float lr,
+                            void* stream) {
+  if (!ctx || !X || !y || n == 0 || epochs < 1 || !(lr >= 0)) return KFVM_ERR_ARG;
+  if (!ctx->gate_loaded) return KFVM_ERR_STATE;
+  const size_t nin = ctx->dims == 2 ? (size_t)Dims<2>::NIN : (size_t)Dims<3>::NIN;
+  constexpr size_t kBatch = 2048;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int e = 0; e < epochs; ++e)
+    for (size_t r0 = 0; r0 < n; r0 += kBatch) {
+      const size_t nb = n - r0 < kBatch ? n - r0 : kBatch;
+      if (launch_gate_train(ctx, X + r0 * nin, y + r0, nb, lr, nullptr, nullptr, st) != cudaSuccess)
+        return KFVM_ERR_CUDA;
+    }
+  return KFVM_OK;
 }
 
 }  // extern "C"

@@ -270,3 +270,34 @@ def test_3d_labels_match_oracle(kfvm, R):
     assert far.mean() > 0.9
     assert np.array_equal(y.cpu().numpy()[far], yr[far])
     assert 0.05 < yr.mean() < 0.95
+
+
+def test_gate_load_float32_and_bfloat16(kfvm):
+    g = kfvm.KFVM([8, 8], dims=2, radius=2)
+    p = ogate.init_params(2, seed=51)
+    g.gate_load(p)
+    assert np.array_equal(g.gate_get_params(), p)
+    bits = (np.ascontiguousarray(ogate.bf16(p).astype(np.float32)).view(np.uint32) >> 16).astype(np.uint16)
+    g.gate_load(bits)
+    assert np.array_equal(g.gate_get_params(), ogate.bf16(p).astype(np.float32))
+    with pytest.raises(kfvm.KfvmError):
+        g.gate_load(p[:-1])
+
+
+def test_gate_train_equals_consecutive_train_steps(kfvm):
+    """kfvm_gate_train: one epoch over 5000 samples = Adam steps on batches 0-2047, 2048-4095, 4096-4999."""
+    rng = np.random.default_rng(52)
+    X = torch.from_numpy(rng.uniform(-1, 1, (5000, 26)).astype(np.float32)).cuda()
+    y = torch.from_numpy((rng.uniform(size=5000) > 0.5).astype(np.float32)).cuda()
+    p = ogate.init_params(2, seed=53)
+    a = kfvm.KFVM([8, 8], dims=2, radius=2)
+    a.gate_set_params(p)
+    a.gate_train(X, y, epochs=1, lr=1e-3)
+    b = kfvm.KFVM([8, 8], dims=2, radius=2)
+    b.gate_set_params(p)
+    for r0 in (0, 2048, 4096):
+        r1 = min(r0 + 2048, 5000)
+        b.gate_train_step(X[r0:r1].contiguous(), y[r0:r1].contiguous(), 1e-3)
+    pa, pb = a.gate_get_params(), b.gate_get_params()
+    assert np.abs(pa - pb).max() <= 1e-6 * np.abs(pb).max() + 1e-7
+    assert np.abs(pa - p).max() > 1e-5  # the parameters moved
