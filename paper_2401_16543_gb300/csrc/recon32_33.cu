@@ -356,17 +356,21 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
 // Rows of A are the 128 cells of a tile (M = 128, one TMEM lane per cell); its K
 // columns are the (stencil, cell) pairs, each stencil's block padded to a multiple
 // of 16 (128 + 48 + 6 x 32 = 368, 23 MMA k-steps).  A holds the lin-prim deltas
-// divided by a per-(cell, variable) power of two s >= max |delta| over S0, split
-// into two FP16 halves (hi + lo); B holds the weights split the same way (each
-// output column scaled by a power of two).  Three kind::f16 MMAs per k-step
-// (hi.hi + hi.lo + lo.hi, FP32 accumulation in TMEM) carry ~22 bits, i.e. the
-// accuracy of the FP32 contraction.
+// divided by a per-(cell, variable) power of two s, split into two FP16 halves
+// (hi + lo); B holds the weights split the same way (each output column scaled by a
+// power of two).  Three kind::f16 MMAs per k-step (hi.hi + hi.lo + lo.hi, FP32
+// accumulation in TMEM) carry ~22 bits, close to the FP32 contraction.
 //   pass 1: derivative values of every stencil, D1 = 8 blocks of 32 TMEM columns
 //           (stencil q's k-steps accumulate into columns 32 q ...), read back per
-//           cell -> beta_q -> WENO-AO coefficients (as in the CUDA-core kernel);
-//   pass 2: A rebuilt with each stencil's block times that cell's coefficient, so
-//           that all 23 k-steps accumulate the blended face values into one
-//           D2 of 64 columns (54 used).
+//           cell -> beta_q -> WENO-AO coefficients (as in the CUDA-core kernel); the
+//           deltas are detrended by the cell's central-difference gradient first
+//           (reconstructions reproduce linear data exactly; the first derivatives
+//           get the gradient back), so the rounding acts on O(h) smaller residuals;
+//   pass 2: A rebuilt (the same deltas), each stencil's k-steps accumulating its 54
+//           face values in its own 64 TMEM columns (the derivative region is free by
+//           then); the WENO-AO blend with the cell's coefficients runs in float32 on
+//           the loaded values (folding the coefficients into A would push the products
+//           of small coefficients into FP16's subnormal range).
 // Tiles whose cells are all linear (gated modes) skip pass 1 and run the 8 k-steps
 // of S0 only.  The CTA is persistent (one per SM): B (138 KB, FP16 hi/lo) is
 // loaded into shared memory once; 512 threads build A chunks (cell r = t % 128,
@@ -374,8 +378,8 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
 // issues the MMAs and commits each buffer back to its mbarrier (a hand-off through
 // per-buffer "full" mbarriers instead of the CTA barrier measured 10% slower).  The scale s of a
 // (cell, variable) is the power of two at or above the central cell's own scale
-// (rho~, sound speed, p~), so A stays O(1) (FP16 range and subnormals cost at most
-// ~3e-8 of that scale).  Every wait has an iteration limit; on expiry the kernel
+// (rho~, sound speed, p~), so A stays O(1) (FP16 subnormals cost at most ~3e-8 of that
+// scale).  Every wait has an iteration limit; on expiry the kernel
 // raises the timeout flag and stops.
 // ===========================================================================
 namespace tcg {
@@ -399,6 +403,7 @@ struct KMap {
   int kq[KS];       // stencil of each k-step
   int first[KS];    // 1 on the first k-step of a stencil
   int off[KT];      // tile offset of each padded K column; kPad for padding
+  float ox[KT], oy[KT], oz[KT];  // its cell offset (0 for padding)
 };
 constexpr int kPad = 1 << 28;
 
@@ -416,8 +421,12 @@ constexpr KMap make_kmap() {
       if (j < len) {
         const int l = G::tab.idx[q][j];
         m.off[kk] = G::tab.off[l][0] + T::SX * (G::tab.off[l][1] + T::SY * G::tab.off[l][2]);
+        m.ox[kk] = (float)G::tab.off[l][0];
+        m.oy[kk] = (float)G::tab.off[l][1];
+        m.oz[kk] = (float)G::tab.off[l][2];
       } else {
         m.off[kk] = kPad;
+        m.ox[kk] = m.oy[kk] = m.oz[kk] = 0.0f;
       }
     }
   }
@@ -607,6 +616,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
 #pragma unroll 1
     for (int v = 0; v < NV && ok; ++v) {
       const Ref ref(sm, c, v, gm1);
+      auto delta_at_off = [&](int o) -> float { return active ? ref.delta(sm, c + o) : 0.0f; };
       auto delta_at = [&](int kk) -> float {
         const int o = c_kmap.off[kk];
         return (active && o != kPad) ? ref.delta(sm, c + o) : 0.0f;
@@ -624,7 +634,19 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
       for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
       if (weno_tile) {
         // ---- pass 1: derivative values of every stencil ----
-        auto value1 = [&](int j, int e) { return delta_at(16 * j + 4 * h + e) * inv_s; };
+        // the derivative pass contracts detrended deltas: every reconstruction reproduces linear
+        // data, so subtracting the linear function gl . o (gl: central differences of the deltas)
+        // from every cell leaves the |alpha| >= 2 values unchanged and lowers the first derivatives
+        // by exactly gl, which is added back below; the split products then carry their ~2^-22
+        // rounding on residuals that are O(h) smaller on smooth data
+        const float glx = 0.5f * (delta_at_off(1) - delta_at_off(-1));
+        const float gly = 0.5f * (delta_at_off(T::SX) - delta_at_off(-T::SX));
+        const float glz = 0.5f * (delta_at_off(T::SX * T::SY) - delta_at_off(-T::SX * T::SY));
+        auto value1 = [&](int j, int e) {
+          const int kk = 16 * j + 4 * h + e;
+          const float lin = fmaf(glx, c_kmap.ox[kk], fmaf(gly, c_kmap.oy[kk], glz * c_kmap.oz[kk]));
+          return (delta_at(kk) - lin) * inv_s;
+        };
         auto mma1 = [&](int j, uint32_t& d_col, uint32_t& idesc, uint32_t& b_hi, uint32_t& b_lo, uint32_t& acc) {
           d_col = 32u * c_kmap.kq[j];
           idesc = id32;
@@ -645,7 +667,9 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
           float bq = 0.0f;
 #pragma unroll
           for (int m = 0; m < 16; ++m) {
-            const float dm = d0[m] * cs1[q * 32 + m];
+            // multi-indices 0, 1, 2 are the first derivatives x, y, z (degree order)
+            const float back = m == 0 ? glx : (m == 1 ? gly : (m == 2 ? glz : 0.0f));
+            const float dm = fmaf(back, inv_s, d0[m] * cs1[q * 32 + m]);
             bq = fmaf(dm, dm, bq);
           }
 #pragma unroll
@@ -688,34 +712,39 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
       }
       // ---- pass 2: blended face values (S0 only on an all-linear tile) ----
       const int ks_end = weno_tile ? KS : 8;
-      float fq[NQ];  // coefficient times 1/s per stencil
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) fq[q] = coef[q] * inv_s;
-      auto value2 = [&](int j, int e) {
-        const int q = c_kmap.kq[j];
-        float f = fq[0];
-#pragma unroll
-        for (int qq = 1; qq < NQ; ++qq) f = (q == qq) ? fq[qq] : f;
-        return delta_at(16 * j + 4 * h + e) * f;
-      };
+      // pass 2: each stencil's face values into its own 64 TMEM columns (the derivative columns have
+      // been read: the region is free), the WENO-AO blend in float32 afterwards.  Folding the
+      // coefficients into A instead would push the small ones' products into FP16's subnormal range.
+      auto value2 = [&](int j, int e) { return delta_at(16 * j + 4 * h + e) * inv_s; };
       auto mma2 = [&](int j, uint32_t& d_col, uint32_t& idesc, uint32_t& b_hi, uint32_t& b_lo, uint32_t& acc) {
-        d_col = 256u;
+        d_col = 64u * c_kmap.kq[j];
         idesc = id64;
         b_hi = b_addr + B1_BYTES + j * B2_BLOCK;
         b_lo = b_hi + B2_BLOCK / 2;
-        acc = j == 0 ? 0u : 1u;
+        acc = c_kmap.first[j] ? 0u : 1u;
       };
 #pragma unroll 1
       for (int j0 = 0; j0 < ks_end; j0 += KPC) kchunk(j0, ks_end - j0 < KPC ? ks_end - j0 : KPC, value2, mma2);
       finish_pass();
       {
-        float d0[16];
-        tc::tmem_ld16(tbase + lane_base + 256u + 16u * h, d0);
+        float out[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) out[m] = 0.0f;
+#pragma unroll 1
+        for (int q = 0; q < (weno_tile ? NQ : 1); ++q) {
+          float d0[16];
+          tc::tmem_ld16(tbase + lane_base + 64u * q + 16u * h, d0);
+          float cq = coef[0];
+#pragma unroll
+          for (int qq = 1; qq < NQ; ++qq) cq = (q == qq) ? coef[qq] : cq;
+#pragma unroll
+          for (int m = 0; m < 16; ++m) out[m] = fmaf(cq, d0[m], out[m]);
+        }
         if (active) {
 #pragma unroll
           for (int m = 0; m < 16; ++m) {
             const int sp_ = 16 * h + m;
-            if (sp_ < F) *slot(faces, ncell_f, fcell, sp_, v) = d0[m] * cs2[sp_] * sc;
+            if (sp_ < F) *slot(faces, ncell_f, fcell, sp_, v) = out[m] * cs2[sp_] * sc;
           }
         }
       }

@@ -38,18 +38,17 @@ def _gated(kfvm, n, bc, tc=1):
     return g
 
 
-@pytest.mark.parametrize("tc,bound", [(0, 1.1), (1, 1.3)])
+@pytest.mark.parametrize("tc,bound", [(0, 1.1), (1, 1.15)])
 def test_smooth_translation_3d_error_not_worse_than_fp64_weno(kfvm, tc, bound):
     """32^3 sine translation (periodic) to t = 0.05: the gated mixed path's L1 density error against
     the exact solution, relative to the plain FP64 WENO-AO path's.  In 3D at radius 3 the shipped
     gate sends only part of the smooth cells (about a quarter here) to the linear reconstruction:
     its training labels come from radius-3 WENO-AO weights, which call much of an evolving 3D flow
     non-smooth, and its inputs see radius 2 plus a summary of the radius-3 shell.  A field that
-    mixes linear and WENO-AO cells measures ~5% above the all-WENO error with the FP32-pipe
-    contraction; the tensor-core contraction (FP16 hi/lo products, ~22 bits against float32's 24)
-    carries ~4x the float32 rounding into the smoothness indicators of WENO cells (mean Riemann-state
-    error 9e-7 against 2.5e-7 on this data), which measures ~25% above.  Neither the 2D gate's gain
-    (a ~10x smaller error) nor the 1e-6 bar holds in this case; the bounds record that."""
+    mixes linear and WENO-AO cells measures 8% (FP32-pipe contraction) / 11% (tensor-core
+    contraction, Riemann states within 1.4x the FP32 pipe's rounding on this data) above the
+    all-WENO error.  Neither the 2D gate's gain (a ~10x smaller error) nor the 1e-6 bar holds in this case;
+    the bound records that."""
     n, t_end = 32, 0.05
     U0 = workloads.sine_3d(n)
     ex = workloads.sine_3d_exact_density(n, t_end)
@@ -62,6 +61,7 @@ def test_smooth_translation_3d_error_not_worse_than_fp64_weno(kfvm, tc, bound):
     gg.run(Ug, 0.4, t_end)
     e64 = np.abs(U64[0].cpu().numpy() - ex).mean()
     eg = np.abs(Ug[0].cpu().numpy() - ex).mean()
+    print(f"3D gated L1 error / FP64 WENO-AO error (tensor cores {tc}): {eg / e64:.4f}")
     assert eg <= e64 * bound, (eg, e64)
 
 
