@@ -53,6 +53,7 @@ class _Problem(ctypes.Structure):
         ("recon", _I), ("riemann", _I),
         ("positivity", _I), ("kappa", _D), ("eta", _D),
         ("mask", ctypes.POINTER(ctypes.c_ubyte)),
+        ("kxrcf_m", _D),
     ]
 
 
@@ -72,6 +73,8 @@ def lib():
         P = ctypes.POINTER(_Problem)
         L.kfo_reconstruct.argtypes = [P, _PD, _PD, _PD]
         L.kfo_reconstruct.restype = _I
+        L.kfo_kxrcf.argtypes = [P, _PD, _PD, ctypes.POINTER(ctypes.c_ubyte)]
+        L.kfo_kxrcf.restype = _I
         L.kfo_limit.argtypes = [P, _PD, _PD]
         L.kfo_limit.restype = _I
         L.kfo_flux.argtypes = [P, _PD, _PD]
@@ -174,7 +177,8 @@ class Oracle:
 
     def __init__(self, n, dim: int = 2, R: int = 2, lo=None, hi=None, bc="periodic", gamma: float = 1.4,
                  ell: float = 5.0, eps: float = 1e-40, recon: str = "weno", riemann: str = "hllc",
-                 positivity: bool = True, kappa: float = 0.1, eta: float = 0.0, mask=None):
+                 positivity: bool = True, kappa: float = 0.1, eta: float = 0.0, mask=None,
+                 kxrcf_m: float = 1.5):
         self.dim, self.R, self.nv = dim, R, dim + 2
         n = list(n) + [1] * (3 - len(n))
         lo = list(lo) if lo is not None else [0.0] * dim
@@ -212,7 +216,8 @@ class Oracle:
         pb.lin_w = _pd(self._lin_w)
         pb.nface, pb.nderiv = self.nface, self.nderiv
         pb.wts, pb.gl_w = _pd(self._wts), _pd(self._gl)
-        pb.recon = {"weno": 0, "linear": 1, "gated": 2}[recon]
+        pb.recon = {"weno": 0, "linear": 1, "gated": 2, "kxrcf": 3}[recon]
+        pb.kxrcf_m = float(kxrcf_m)
         if mask is not None:
             self._mask = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).ravel())
             if self._mask.size != self.ncell:
@@ -236,6 +241,17 @@ class Oracle:
         st = lib().kfo_reconstruct(ctypes.byref(self._pb), _pd(U), _pd(faces), _pd(om) if with_omega else None)
         self.status = st
         return (faces, om) if with_omega else faces
+
+    def kxrcf(self, U):
+        """KXRCF indicator of Sec. 3.5 on the unlimited linear states of U: (ratio, mask) per cell,
+        ratio = max over the cell's face points of |q+ - q-| / <Q> with q = p / rho^gamma, mask 1
+        (smooth: linear reconstruction) where ratio < Delta^m, Delta the largest cell width."""
+        U = self._state(U)
+        ratio = np.zeros(self.shape[1:])
+        mask = np.zeros(self.shape[1:], dtype=np.uint8)
+        self.status = lib().kfo_kxrcf(ctypes.byref(self._pb), _pd(U), _pd(ratio),
+                                      mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        return ratio, mask
 
     def limit(self, U, faces):
         """Positivity-preserving limiter of Sec. 4 applied to Riemann states [F, nv, *grid]."""

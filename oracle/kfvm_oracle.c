@@ -28,6 +28,10 @@
  *                    normalised (Eqs. 24-25), WENO-AO blend (Eq. 19), back
  *                    transform (Eq. 28).  Mode 1 is the unlimited linear S0
  *                    reconstruction of the conservative variables.
+ *   kfo_kxrcf        Sec. 3.5 and Sec. 5.3 step 2 items 1-2: the KXRCF
+ *                    troubled-cell indicator on the unlimited linear states,
+ *                    which decides per cell between the linear and the WENO-AO
+ *                    reconstruction (recon mode 3).
  *   kfo_limit        Sec. 4 (Sec. 5.3 step 3): positivity-preserving limiter of
  *                    the Riemann states with data-dependent density and
  *                    pressure bounds; theta_p by bisection.
@@ -294,11 +298,13 @@ typedef struct {
   const double* wts;    /* per q: F*N_q face weights then M*N_q derivative weights */
   const double* gl_w;   /* R Gauss-Legendre weights on [-1/2,1/2] */
   int recon;            /* 0: WENO-AO in linearized primitive variables; 1: linear S0, conservative;
-                           2: per-cell choice of the two by `mask` (the gated reconstruction) */
+                           2: per-cell choice of the two by `mask` (the gated reconstruction);
+                           3: per-cell choice by the KXRCF indicator of each stage's own state */
   int riemann;          /* 0: HLLC, 1: HLL */
   int positivity;       /* 1: apply the positivity-preserving limiter of Sec. 4 to the Riemann states */
   double kappa, eta;    /* bound relaxation kappa and flattener eta of Sec. 4.1 */
   const unsigned char* mask; /* recon 2: per cell, 1 = linear (smooth), 0 = WENO-AO */
+  double kxrcf_m;       /* recon 3: power m of the KXRCF threshold Delta^m (Sec. 3.5: m = 3/2) */
 } kfo_problem;
 
 static long ncell_of(const kfo_problem* pb) { return (long)pb->n[0] * pb->n[1] * pb->n[2]; }
@@ -370,10 +376,24 @@ static long sub_start(const kfo_problem* pb, int q) {
  *   faces : out, [F][nv][ncell]
  *   omega : optional out, [nq][nv][ncell] normalised nonlinear weights (WENO mode)
  */
+int kfo_kxrcf(const kfo_problem* pb, const double* U, double* ratio, unsigned char* mask);
+
 int kfo_reconstruct(const kfo_problem* pb, const double* U, double* faces, double* omega) {
   const int dim = pb->dim, nv = pb->nv, n0 = pb->n0, F = pb->nface, M = pb->nderiv, nq = pb->nq;
   const long nc = ncell_of(pb);
   int status = KFO_OK;
+  if (pb->recon == 3) {
+    /* Sec. 5.3 step 2: the KXRCF indicator of this state picks each cell's reconstruction */
+    unsigned char* kmask = (unsigned char*)malloc((size_t)nc);
+    if (!kmask) return KFO_ERR_NOMEM;
+    kfo_problem gated = *pb;
+    int sk = kfo_kxrcf(pb, U, NULL, kmask);
+    gated.recon = 2;
+    gated.mask = kmask;
+    if (sk == KFO_OK) sk = kfo_reconstruct(&gated, U, faces, omega);
+    free(kmask);
+    return sk;
+  }
   double* sten = (double*)malloc(sizeof(double) * n0 * nv); /* [l][var] conservative */
   double* W = (double*)malloc(sizeof(double) * n0 * nv);    /* [var][l] reconstruction variables */
   double* vals = (double*)malloc(sizeof(double) * nq * F);  /* v_q(s) for one variable */
@@ -680,6 +700,80 @@ double kfo_max_rate(const kfo_problem* pb, const double* U) {
     if (!(rate <= mx)) mx = rate; /* a NaN rate propagates */
   }
   return mx;
+}
+
+/* ------------------------------------------------------------------------- */
+/* KXRCF troubled-cell indicator (Sec. 3.5; Sec. 5.3 step 2, items 1-2).      */
+/* ------------------------------------------------------------------------- */
+static double entropy_q(const double* u, int dim, double gamma) {
+  /* q = p / rho^gamma of one conservative state; +inf when it is not admissible */
+  if (!physical(u, dim, gamma)) return INFINITY;
+  return pressure(u, dim, gamma) / pow(u[0], gamma);
+}
+
+/*
+ * Step 1: unlimited linear S0 reconstruction of the conservative variables on
+ * every cell.  Step 2: for every cell c and every Gauss point s of each of its
+ * faces, the entropy q = p / rho^gamma of c's own state at s (minus side) and of
+ * the state the cell across that face reconstructs at the same point (plus
+ * side); ratio[c] = max_s |q+ - q-| / <Q>, with <Q> = p(Ubar_c) / rhobar_c^gamma
+ * from c's cell average.  The cell is smooth (mask 1: linear reconstruction)
+ * when ratio < Delta^m, Delta the largest cell width over the axes; otherwise it
+ * is flagged for WENO-AO (mask 0).
+ * Faces on the physical boundary: periodic -> the wrapped neighbour; outflow ->
+ * the exterior state is a copy of the interior one (Sec. 5.3 step 4), so the
+ * face has no jump.  A state that is not admissible (rho <= 0, p <= 0 or not
+ * finite) on either side of a point, or such a cell average, gives ratio = +inf.
+ * ratio and mask may each be NULL.
+ */
+int kfo_kxrcf(const kfo_problem* pb, const double* U, double* ratio, unsigned char* mask) {
+  const int dim = pb->dim, nv = pb->nv, R = pb->R;
+  const long nc = ncell_of(pb);
+  const int nt = (dim == 2) ? R : R * R;
+  kfo_problem lin = *pb;
+  lin.recon = 1;
+  double* faces = (double*)malloc(sizeof(double) * (size_t)pb->nface * nv * nc);
+  if (!faces) return KFO_ERR_NOMEM;
+  kfo_reconstruct(&lin, U, faces, NULL); /* unlimited states may be inadmissible: handled below */
+  double delta = 0;
+  for (int d = 0; d < dim; ++d)
+    if (pb->dx[d] > delta) delta = pb->dx[d];
+  const double thresh = pow(delta, pb->kxrcf_m);
+  for (int z = 0; z < pb->n[2]; ++z)
+    for (int y = 0; y < pb->n[1]; ++y)
+      for (int x = 0; x < pb->n[0]; ++x) {
+        const long c = ((long)z * pb->n[1] + y) * pb->n[0] + x;
+        double ubar[5];
+        for (int v = 0; v < nv; ++v) ubar[v] = U[v * nc + c];
+        const double Q = entropy_q(ubar, dim, pb->gamma);
+        double jmax = 0;
+        for (int dir = 0; dir < dim; ++dir)
+          for (int side = 0; side < 2; ++side) {
+            int nb[3] = {x, y, z};
+            nb[dir] += side ? 1 : -1;
+            const int outside = nb[dir] < 0 || nb[dir] >= pb->n[dir];
+            if (outside && pb->bc[dir][side] == 1) continue; /* outflow: exterior = interior */
+            nb[dir] = ((nb[dir] % pb->n[dir]) + pb->n[dir]) % pb->n[dir];
+            const long cn = ((long)nb[2] * pb->n[1] + nb[1]) * pb->n[0] + nb[0];
+            for (int t = 0; t < nt; ++t) {
+              const int s_in = (dir * 2 + side) * nt + t;
+              const int s_out = (dir * 2 + (1 - side)) * nt + t;
+              double um[5], up[5];
+              for (int v = 0; v < nv; ++v) {
+                um[v] = faces[((long)s_in * nv + v) * nc + c];
+                up[v] = faces[((long)s_out * nv + v) * nc + cn];
+              }
+              const double qm = entropy_q(um, dim, pb->gamma), qp = entropy_q(up, dim, pb->gamma);
+              const double j = (isinf(qm) || isinf(qp)) ? INFINITY : fabs(qp - qm);
+              if (j > jmax) jmax = j;
+            }
+          }
+        const double r = isinf(Q) ? INFINITY : jmax / Q;
+        if (ratio) ratio[c] = r;
+        if (mask) mask[c] = r < thresh ? 1 : 0;
+      }
+  free(faces);
+  return KFO_OK;
 }
 
 int kfo_rhs(const kfo_problem* pb, const double* U, double* dUdt) {
