@@ -101,7 +101,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--path", choices=["auto", "fp64", "fp32", "gated"], default="auto")
+    ap.add_argument("--path", choices=["auto", "fp64", "fp32", "gated", "kxrcf"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline path only (no other paths, e2e or CPU baseline): for profiler runs")
@@ -235,8 +235,10 @@ def make_solver(W, path, n=None):
 
     from paper_2401_16543_gb300 import KFVM
     g = KFVM(list(n or W.n), dims=W.dims, radius=W.R, bc=W.bc)
-    if path in ("fp32", "gated"):
+    if path in ("fp32", "gated", "kxrcf"):
         g.set_option("precision", 32)
+    if path == "kxrcf":  # the paper's troubled-cell indicator (Sec. 3.5) instead of the learned gate
+        g.set_option("recon", 4)
     if path == "gated":
         g.gate_set_params(np.load(W.gate_path()))
         g.set_option("gate_threshold", GATE_THRESHOLD)
@@ -380,7 +382,7 @@ def main():
 
     # ---- the other paths on the same workload (plain FP64 is the metric's reference) ----
     others = {}
-    for other in ("fp64", "fp32", "gated"):
+    for other in ("fp64", "fp32", "gated", "kxrcf"):
         if args.headline_only or other == path or (other == "gated" and not W.has_gate()):
             continue
         k = max(3, args.steps // 4)
@@ -391,11 +393,15 @@ def main():
             n_o = W.n[:2] + [W.fp64_planes]
             note = f"first {W.fp64_planes} z-planes of the state ({W.n[0]}x{W.n[1]}x{W.fp64_planes} cells)"
             k = 1
-        _, mso, _, _, _ = measure_path(W, other, Uo0, k, 1 if other == "fp64" else 2, stream, flush_buf, n_o,
-                                       barrier=barrier)
+        go, mso, _, _, _ = measure_path(W, other, Uo0, k, 1 if other == "fp64" else 2, stream, flush_buf, n_o,
+                                        barrier=barrier)
         mso = job_time_ms(mso, dist, dev)
         cells = ncell if n_o is None else n_o[0] * n_o[1] * n_o[2]
         others[other] = {"value": job_value(world, cells, k, mso), "ms_per_step": mso / k, "steps": k}
+        if other in ("gated", "kxrcf"):  # share of cells the indicator sends to the linear reconstruction
+            m = go.gate_mask(Uo0) if other == "gated" else go.kxrcf_mask(Uo0)
+            others[other]["smooth_fraction_initial_state"] = round(float(m.float().mean().item()), 4)
+        del go
         print(f"[bench] {other}: {mso / k:.3f} ms per step", file=sys.stderr, flush=True)
         if note:
             others[other]["sample"] = note
@@ -430,12 +436,13 @@ def main():
     mode = "weno" if path in ("fp64", "fp32") else "gated"
     flops = algo_flops_per_cell(W.dims, W.R, "weno") * ncell
     smooth_frac = None
-    if path == "gated":
+    if path in ("gated", "kxrcf"):
         # WENO cells at WENO cost, gated cells at the linear reconstruction's cost, averaged over
         # the masks of the initial and the final state of the timed run
         fr = []
         for Us in (U0, g_final_state):
-            fr.append(float(g.gate_mask(Us).float().mean().item()))
+            m = g.gate_mask(Us) if path == "gated" else g.kxrcf_mask(Us)
+            fr.append(float(m.float().mean().item()))
         smooth_frac = sum(fr) / len(fr)
         flops = ncell * (smooth_frac * algo_flops_per_cell(W.dims, W.R, "linear")
                          + (1 - smooth_frac) * algo_flops_per_cell(W.dims, W.R, "weno"))
@@ -485,7 +492,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "gated": "f32+bf16"}[path],
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "gated": "f32+bf16", "kxrcf": "f32"}[path],
             "data": "synthetic",
             "config": {"workload": W.desc, "name": W.name, "grid": W.n, "radius": W.R, "path": path,
                        "gate": ({"params": f"paper_2401_16543_gb300/{W.gate}",

@@ -113,7 +113,11 @@ size_t kfvm_weights_count(const kfvm_ctx* ctx);
  *                 (default; Sec. 3, Sec. 5.3), 1 unlimited linear S0
  *                 reconstruction of the conservative variables on every cell
  *                 (Sec. 5.3 step 2a), 2 gated: cells the gate network marks
- *                 smooth take the linear reconstruction, the others WENO-AO.
+ *                 smooth take the linear reconstruction, the others WENO-AO,
+ *                 4 KXRCF: the paper's troubled-cell indicator (Sec. 3.5,
+ *                 evaluated as in Sec. 5.3 step 2 items 1-2; kfvm_kxrcf_mask)
+ *                 picks each cell's reconstruction from every stage's own
+ *                 state, cells it does not flag take the linear one.
  *   "riemann"     0 HLLC (default), 1 HLL; Batten wave speeds (Sec. 5.4).
  *   "positivity"  1 (default) apply the positivity-preserving limiter of
  *                 Sec. 4 to the Riemann states; 0 off.
@@ -121,6 +125,8 @@ size_t kfvm_weights_count(const kfvm_ctx* ctx);
  *   "eps"         epsilon of the nonlinear weights, Eq. 24 (1e-40).
  *                 (3 is set by kfvm_set_smooth_mask: gated by a caller mask.)
  *   "gate_threshold"  probability above which a cell is treated as smooth (0.5).
+ *   "kxrcf_m"     power m of the KXRCF threshold Delta^m (Sec. 3.5: 3/2),
+ *                 0 < m <= 16.
  *   "tensor_cores" 1 (default) / 0: in the FP32 mode with dims = 3, radius 3,
  *                 run the stencil contraction on the tcgen05 tensor cores (FP16
  *                 hi/lo split operands, FP32 accumulation in tensor memory) or
@@ -204,6 +210,31 @@ kfvm_status kfvm_step(kfvm_ctx* ctx, double* U, double cfl, double t_remaining, 
 
 /* Synchronise the stream and return (and clear) the device status flag. */
 kfvm_status kfvm_sync_status(kfvm_ctx* ctx, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Troubled-cell indicator (Sec. 3.5): which cells need WENO-AO               */
+/* ------------------------------------------------------------------------- */
+
+/* The KXRCF troubled-cell indicator of Sec. 3.5, adapted there from
+ * discontinuous Galerkin methods, evaluated as in Sec. 5.3 step 2 items 1-2.
+ * Every cell of U gets its unlimited linear S0 reconstruction of the
+ * conservative variables at its face Gauss points; at each point s of the
+ * cell's faces the entropy q = p / rho^gamma of that state and of the state
+ * the cell across the face reconstructs at the same point are compared, and
+ * the cell is smooth when  max_s |q+ - q-| / <Q>  <  Delta^m  with
+ * <Q> = p / rho^gamma of the cell average, Delta the largest cell width and m
+ * the "kxrcf_m" option.  Faces on an outflow boundary carry no jump (the
+ * exterior state copies the interior one, Sec. 5.3 step 4), periodic faces
+ * compare with the wrapped neighbour; a non-admissible state (rho <= 0,
+ * p <= 0, not finite) at a point or in the average flags the cell.
+ * mask_out: device, one byte per cell in the state's cell order, 1 = smooth
+ * (linear reconstruction), 0 = flagged (WENO-AO).  In the FP32 mode the
+ * reconstruction and the comparison run in float32 on the float32 copy of U,
+ * as the "recon" 4 step does; in the FP64 mode in float64 on U.  The
+ * library's scratch (the float32 copy) is overwritten; nothing is allocated.
+ * Errors: KFVM_ERR_ARG (null pointer), KFVM_ERR_STATE (weights not built),
+ * KFVM_ERR_CUDA (launch). */
+kfvm_status kfvm_kxrcf_mask(kfvm_ctx* ctx, const double* U, unsigned char* mask_out, void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* Learned gate (an extension, no counterpart in the paper; it plays the role  */

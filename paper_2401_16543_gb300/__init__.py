@@ -67,6 +67,7 @@ def load():
     L.kfvm_gate_forward.argtypes = [P, P, P, S, P]
     L.kfvm_set_smooth_mask.argtypes = [P, P, P]
     L.kfvm_gate_mask.argtypes = [P, P, P, P]
+    L.kfvm_kxrcf_mask.argtypes = [P, P, P, P]
     L.kfvm_gate_train_step.argtypes = [P, P, P, S, ctypes.c_float, P, P, P]
     L.kfvm_gate_load.argtypes = [P, P, S]
     L.kfvm_gate_train.argtypes = [P, P, P, S, I, ctypes.c_float, P]
@@ -310,6 +311,15 @@ class KFVM:
         U = self._state(U)
         m = torch.empty(self.shape[1:], dtype=torch.uint8, device=U.device)
         _check(self._L.kfvm_gate_mask(self._ctx, _ptr(U), _ptr(m), _stream(stream)), "kfvm_gate_mask")
+        return m
+
+    def kxrcf_mask(self, U, stream=None):
+        """The KXRCF indicator's smooth mask of U (uint8 per cell, 1 = linear), as the "recon" 4 step
+        computes it: from the float32 copy of U in the FP32 mode, from U in the FP64 mode."""
+        import torch
+        U = self._state(U)
+        m = torch.empty(self.shape[1:], dtype=torch.uint8, device=U.device)
+        _check(self._L.kfvm_kxrcf_mask(self._ctx, _ptr(U), _ptr(m), _stream(stream)), "kfvm_kxrcf_mask")
         return m
 
     def set_smooth_mask(self, mask, stream=None):

@@ -395,7 +395,7 @@ kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double v) {
     if (v != 64 && v != 32) return KFVM_ERR_ARG;
     ctx->precision = (int)v;
   } else if (k == "recon") {
-    if (v != 0 && v != 1 && v != 2) return KFVM_ERR_ARG;
+    if (v != 0 && v != 1 && v != 2 && v != 4) return KFVM_ERR_ARG;
     ctx->recon = (int)v;
   } else if (k == "riemann") {
     if (v != 0 && v != 1) return KFVM_ERR_ARG;
@@ -426,6 +426,9 @@ kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double v) {
   } else if (k == "profile") {
     if (v != 0 && v != 1) return KFVM_ERR_ARG;
     ctx->profile = (int)v;
+  } else if (k == "kxrcf_m") {
+    if (!(v > 0 && v <= 16)) return KFVM_ERR_ARG;
+    ctx->kxrcf_m = v;
   } else if (k == "gate_threshold") {
     if (!(v > 0 && v < 1)) return KFVM_ERR_ARG;
     ctx->gate_threshold = v;
@@ -442,9 +445,12 @@ kfvm_status kfvm_reconstruct(kfvm_ctx* ctx, const double* U, void* faces, void* 
   cudaStream_t st = (cudaStream_t)stream;
   if (ctx->precision == 64) {
     if (ctx->recon == 2) KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, U, nullptr, st));
+    if (ctx->recon == 4) KFVM_LAUNCH(ctx, kProfKxrcf, st, launch_kxrcf(ctx, U, nullptr, ctx->d_gate_mask, st));
     KFVM_LAUNCH(ctx, kProfRecon64, st, launch_recon64(ctx, U, (double*)faces, st));
   } else {
     KFVM_LAUNCH(ctx, kProfShadow, st, launch_shadow(ctx, U, ctx->d_shadow, st));
+    if (ctx->recon == 4)
+      KFVM_LAUNCH(ctx, kProfKxrcf, st, launch_kxrcf(ctx, U, ctx->d_shadow, ctx->d_gate_mask, st));
     // the FP32 reconstruction evaluates the learned gate itself (fused)
     KFVM_LAUNCH(ctx, kProfRecon32, st, launch_recon32(ctx, U, ctx->d_shadow, (float*)faces, st));
   }
@@ -502,8 +508,11 @@ kfvm_status kfvm_rhs(kfvm_ctx* ctx, const double* U, double* dUdt, void* stream)
   cudaStream_t st = (cudaStream_t)stream;
   if (ctx->precision == 64) {
     if (ctx->recon == 2) KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, U, nullptr, st));
+    if (ctx->recon == 4) KFVM_LAUNCH(ctx, kProfKxrcf, st, launch_kxrcf(ctx, U, nullptr, ctx->d_gate_mask, st));
   } else {
     KFVM_LAUNCH(ctx, kProfShadow, st, launch_shadow(ctx, U, ctx->d_shadow, st));
+    if (ctx->recon == 4)
+      KFVM_LAUNCH(ctx, kProfKxrcf, st, launch_kxrcf(ctx, U, ctx->d_shadow, ctx->d_gate_mask, st));
   }
   return stage_pass(ctx, 0, U, nullptr, dUdt, ctx->d_shadow, nullptr, st);
 }
@@ -532,12 +541,27 @@ kfvm_status kfvm_step(kfvm_ctx* ctx, double* U, double cfl, double t_remaining, 
   for (int k = 0; k < 3; ++k) {
     if (ctx->recon == 2 && !fp32)  // the FP32 reconstruction evaluates the gate itself
       KFVM_LAUNCH(ctx, kProfGateMask, st, launch_gate_mask(ctx, in[k], nullptr, st));
+    if (ctx->recon == 4)  // the indicator of this stage's input state, for the whole grid
+      KFVM_LAUNCH(ctx, kProfKxrcf, st, launch_kxrcf(ctx, in[k], fp32 ? sh_in[k] : nullptr, ctx->d_gate_mask, st));
     s = stage_pass(ctx, k + 1, in[k], U, outp[k], sh_in[k], sh_out[k], st);
     if (s) return s;
   }
   if (dt_out) {
     KFVM_TRY(cudaMemcpyAsync(dt_out, &ctx->d_scalars->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
     return kfvm_sync_status(ctx, stream);
+  }
+  return KFVM_OK;
+}
+
+kfvm_status kfvm_kxrcf_mask(kfvm_ctx* ctx, const double* U, unsigned char* mask_out, void* stream) {
+  if (!ctx || !U || !mask_out) return KFVM_ERR_ARG;
+  if (!ctx->weights_built) return KFVM_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ctx->precision == 32) {
+    KFVM_LAUNCH(ctx, kProfShadow, st, launch_shadow(ctx, U, ctx->d_shadow, st));
+    KFVM_LAUNCH(ctx, kProfKxrcf, st, launch_kxrcf(ctx, U, ctx->d_shadow, mask_out, st));
+  } else {
+    KFVM_LAUNCH(ctx, kProfKxrcf, st, launch_kxrcf(ctx, U, nullptr, mask_out, st));
   }
   return KFVM_OK;
 }
@@ -559,7 +583,7 @@ int kfvm_profile_count(void) { return kProfCount; }
 
 kfvm_status kfvm_profile_get(kfvm_ctx* ctx, int index, const char** name, long long* launches, double* ms) {
   static const char* names[kProfCount] = {"max_rate", "recon64", "recon32", "face_flux", "flux_update",
-                                          "gate_mask", "shadow"};
+                                          "gate_mask", "shadow", "kxrcf"};
   if (!ctx || index < 0 || index >= kProfCount) return KFVM_ERR_ARG;
   const bool done = prof_fold(ctx);
   if (name) *name = names[index];

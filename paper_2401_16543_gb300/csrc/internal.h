@@ -25,7 +25,7 @@ struct DevScalars {
 
 // Kernel families timed by the "profile" option.
 enum ProfKernel : int { kProfMaxRate = 0, kProfRecon64, kProfRecon32, kProfFaceFlux, kProfUpdate, kProfGateMask,
-                        kProfShadow, kProfCount };
+                        kProfShadow, kProfKxrcf, kProfCount };
 
 struct ProfPair {
   cudaEvent_t start, stop;
@@ -55,6 +55,7 @@ struct kfvm_ctx {
   int tensor_cores = 1;  // d = 3, R = 3 FP32 contraction on tcgen05 (0: the CUDA-core kernel)
   int timeout_probe = 0;  // test hook: the next tensor-core launch waits on nothing and times out
   double kappa = 0.1, eta = 0.0, eps = 1e-40, gate_threshold = 0.5;
+  double kxrcf_m = 1.5;  // power m of the KXRCF threshold Delta^m (recon mode 4)
   // weights
   size_t wcount = 0;
   bool weights_built = false;
@@ -122,6 +123,10 @@ cudaError_t launch_flux_update(kfvm_ctx* ctx, int stage, const void* faces, cons
                                int zc_hi = 0, int zf_first = 0, int zf_count = 0);
 // shadow != nullptr: features from the float32 shadow (mixed path), else from U
 cudaError_t launch_gate_mask(kfvm_ctx* ctx, const double* U, const float* shadow, cudaStream_t st);
+// KXRCF troubled-cell mask of U (shadow != nullptr: from the float32 shadow, the FP32 path).
+cudaError_t launch_kxrcf(kfvm_ctx* ctx, const double* U, const float* shadow, unsigned char* mask, cudaStream_t st);
+// The reconstruction kernels' mode: the KXRCF mode (4) runs them on the indicator's mask (3).
+inline int kernel_recon_mode(const kfvm_ctx* c) { return c->recon == 4 ? 3 : c->recon; }
 // WENO-AO training labels of the gate (float32 shadow input).
 cudaError_t launch_labels(kfvm_ctx* ctx, const double* U, float* y, float thresh, cudaStream_t st);
 cudaError_t launch_gate_features(kfvm_ctx* ctx, const double* U, float* X, float* y, double tau, cudaStream_t st);

@@ -669,7 +669,7 @@ cudaError_t launch(kfvm_ctx* ctx, const double* U, const float* shadow, float* f
   for (int i = 0; i < G::WCOUNT; ++i) wp->w[i] = (float)ctx->w_host[i];
   const float th = (float)ctx->gate_threshold;
   const float zth = logf(th / (1.0f - th));
-  kern<<<tiles, T::THREADS, smem, st>>>(a, ctx->recon, U, shadow, faces, ctx->d_gate_mask,
+  kern<<<tiles, T::THREADS, smem, st>>>(a, kernel_recon_mode(ctx), U, shadow, faces, ctx->d_gate_mask,
                                         (const gate::Pack<D>*)ctx->d_gate_pack, zth, *wp);
   ctx->launches += 1;
   return cudaGetLastError();

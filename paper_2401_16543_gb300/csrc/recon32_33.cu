@@ -362,10 +362,7 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
 // accumulation in TMEM) carry ~22 bits, close to the FP32 contraction.
 //   pass 1: derivative values of every stencil, D1 = 8 blocks of 32 TMEM columns
 //           (stencil q's k-steps accumulate into columns 32 q ...), read back per
-//           cell -> beta_q -> WENO-AO coefficients (as in the CUDA-core kernel); the
-//           deltas are detrended by the cell's central-difference gradient first
-//           (reconstructions reproduce linear data exactly; the first derivatives
-//           get the gradient back), so the rounding acts on O(h) smaller residuals;
+//           cell -> beta_q -> WENO-AO coefficients (as in the CUDA-core kernel);
 //   pass 2: A rebuilt (the same deltas), each stencil's k-steps accumulating its 54
 //           face values in its own 64 TMEM columns (the derivative region is free by
 //           then); the WENO-AO blend with the cell's coefficients runs in float32 on
@@ -403,7 +400,6 @@ struct KMap {
   int kq[KS];       // stencil of each k-step
   int first[KS];    // 1 on the first k-step of a stencil
   int off[KT];      // tile offset of each padded K column; kPad for padding
-  float ox[KT], oy[KT], oz[KT];  // its cell offset (0 for padding)
 };
 constexpr int kPad = 1 << 28;
 
@@ -421,12 +417,8 @@ constexpr KMap make_kmap() {
       if (j < len) {
         const int l = G::tab.idx[q][j];
         m.off[kk] = G::tab.off[l][0] + T::SX * (G::tab.off[l][1] + T::SY * G::tab.off[l][2]);
-        m.ox[kk] = (float)G::tab.off[l][0];
-        m.oy[kk] = (float)G::tab.off[l][1];
-        m.oz[kk] = (float)G::tab.off[l][2];
       } else {
         m.off[kk] = kPad;
-        m.ox[kk] = m.oy[kk] = m.oz[kk] = 0.0f;
       }
     }
   }
@@ -616,7 +608,6 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
 #pragma unroll 1
     for (int v = 0; v < NV && ok; ++v) {
       const Ref ref(sm, c, v, gm1);
-      auto delta_at_off = [&](int o) -> float { return active ? ref.delta(sm, c + o) : 0.0f; };
       auto delta_at = [&](int kk) -> float {
         const int o = c_kmap.off[kk];
         return (active && o != kPad) ? ref.delta(sm, c + o) : 0.0f;
@@ -634,19 +625,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
       for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
       if (weno_tile) {
         // ---- pass 1: derivative values of every stencil ----
-        // the derivative pass contracts detrended deltas: every reconstruction reproduces linear
-        // data, so subtracting the linear function gl . o (gl: central differences of the deltas)
-        // from every cell leaves the |alpha| >= 2 values unchanged and lowers the first derivatives
-        // by exactly gl, which is added back below; the split products then carry their ~2^-22
-        // rounding on residuals that are O(h) smaller on smooth data
-        const float glx = 0.5f * (delta_at_off(1) - delta_at_off(-1));
-        const float gly = 0.5f * (delta_at_off(T::SX) - delta_at_off(-T::SX));
-        const float glz = 0.5f * (delta_at_off(T::SX * T::SY) - delta_at_off(-T::SX * T::SY));
-        auto value1 = [&](int j, int e) {
-          const int kk = 16 * j + 4 * h + e;
-          const float lin = fmaf(glx, c_kmap.ox[kk], fmaf(gly, c_kmap.oy[kk], glz * c_kmap.oz[kk]));
-          return (delta_at(kk) - lin) * inv_s;
-        };
+        auto value1 = [&](int j, int e) { return delta_at(16 * j + 4 * h + e) * inv_s; };
         auto mma1 = [&](int j, uint32_t& d_col, uint32_t& idesc, uint32_t& b_hi, uint32_t& b_lo, uint32_t& acc) {
           d_col = 32u * c_kmap.kq[j];
           idesc = id32;
@@ -667,9 +646,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
           float bq = 0.0f;
 #pragma unroll
           for (int m = 0; m < 16; ++m) {
-            // multi-indices 0, 1, 2 are the first derivatives x, y, z (degree order)
-            const float back = m == 0 ? glx : (m == 1 ? gly : (m == 2 ? glz : 0.0f));
-            const float dm = fmaf(back, inv_s, d0[m] * cs1[q * 32 + m]);
+            const float dm = d0[m] * cs1[q * 32 + m];
             bq = fmaf(dm, dm, bq);
           }
 #pragma unroll
@@ -872,7 +849,7 @@ cudaError_t launch_recon32_33_tc(kfvm_ctx* ctx, const double* U, const float* sh
   const float th = (float)ctx->gate_threshold;
   const float zth = logf(th / (1.0f - th));
   tcg::recon33_tc_kernel<<<grid, tcg::TCT, tcg::TSmem::total, st>>>(
-      a, ctx->recon, ntiles, U, shadow, faces, ctx->d_gate_mask, (const gate::Pack<3>*)ctx->d_gate_pack, zth,
+      a, kernel_recon_mode(ctx), ntiles, U, shadow, faces, ctx->d_gate_mask, (const gate::Pack<3>*)ctx->d_gate_pack, zth,
       reinterpret_cast<const uint4*>(ctx->d_w33tc), ctx->timeout_probe);
   ctx->timeout_probe = 0;
   ctx->launches += 1;
@@ -897,7 +874,7 @@ cudaError_t launch_recon32_33(kfvm_ctx* ctx, const double* U, const float* shado
   if (e != cudaSuccess) return e;
   const float th = (float)ctx->gate_threshold;
   const float zth = logf(th / (1.0f - th));
-  recon33_kernel<<<tiles, TH, smem, st>>>(a, ctx->recon, U, shadow, faces, ctx->d_gate_mask,
+  recon33_kernel<<<tiles, TH, smem, st>>>(a, kernel_recon_mode(ctx), U, shadow, faces, ctx->d_gate_mask,
                                           (const gate::Pack<3>*)ctx->d_gate_pack, zth,
                                           reinterpret_cast<const float4*>(ctx->d_w32));
   ctx->launches += 1;

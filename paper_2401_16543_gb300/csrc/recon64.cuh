@@ -387,7 +387,7 @@ cudaError_t launch_dr(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_
     for (int i = 0; i < Geo<D, R>::WCOUNT; ++i) wp->w[i] = ctx->w_host[i];
   else
     wp->w[0] = 0.0;
-  kern<<<tiles, TS, smem, st>>>(a, ctx->recon, U, faces, ctx->d_gate_mask, ctx->d_w64, *wp);
+  kern<<<tiles, TS, smem, st>>>(a, kernel_recon_mode(ctx), U, faces, ctx->d_gate_mask, ctx->d_w64, *wp);
   ctx->launches += 1;
   return cudaGetLastError();
 }

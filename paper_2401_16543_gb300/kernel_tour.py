@@ -5,7 +5,8 @@
 Launches, in order: the FP64 path (build_weights, max_rate, recon64, flux_update) and the flux-only
 entry (face_flux, update) on 2D 256^2; the FP32 path in 3D radius 2 (shadow, recon32<3,2>,
 flux_update) on 48^3; 3D radius 3 on 32^3 (recon33 on the FP32 pipe, recon33_tc on the tensor
-cores, label33); the learned gate (features, label, forward, mask, train, adam) on the 2D grid.
+cores, label33); the learned gate (features, label, forward, mask, train, adam) and the KXRCF
+indicator (float64 and float32) on the 2D grid.
 Every computation goes through the C ABI; results are not checked here (the tests do that).
 """
 from __future__ import annotations
@@ -41,6 +42,11 @@ def main() -> None:
     g.set_option("precision", 64)
     g.set_option("recon", 2)
     g.gate_mask(U2)
+    # the KXRCF troubled-cell indicator (Sec. 3.5) in both precisions
+    g.kxrcf_mask(U2)
+    g.set_option("precision", 32)
+    g.kxrcf_mask(U2)
+    g.set_option("precision", 64)
     # FP32 path, 3D radius 2
     U3 = workloads.half_sine_voronoi_3d(48, k=8, seed=3, device=dev).contiguous()
     h = KFVM([48, 48, 48], dims=3, radius=2, bc="periodic")
