@@ -61,16 +61,10 @@ __host__ __device__ constexpr int max_ext() {
   return m;
 }
 
-template <class T>
-__device__ __forceinline__ T pow_t(T x, T y);
-template <>
-__device__ __forceinline__ double pow_t<double>(double x, double y) {
-  return pow(x, y);
-}
-template <>
-__device__ __forceinline__ float pow_t<float>(float x, float y) {
-  return powf(x, y);
-}
+// rho^-gamma: float64 through pow; float32 as 2^(-gamma log2 rho) with the hardware log2 and exp2
+// (relative error ~2e-7, below the float32 copy's own rounding of the states it is applied to)
+__device__ __forceinline__ double rho_pow_neg(double rho, double gamma) { return 1.0 / pow(rho, gamma); }
+__device__ __forceinline__ float rho_pow_neg(float rho, float gamma) { return exp2f(-gamma * __log2f(rho)); }
 
 // q = p / rho^gamma of a conservative state; +inf when it is not admissible
 template <int D, class T>
@@ -80,7 +74,7 @@ __device__ __forceinline__ T entropy(const T* u, T gamma) {
   for (int k = 0; k < D; ++k) m2 = fma(u[1 + k], u[1 + k], m2);
   const T p = (gamma - T(1)) * (u[D + 1] - T(0.5) * m2 / u[0]);
   const bool ok = u[0] > T(0) && p > T(0) && isfinite(p) && isfinite(u[0]);
-  return ok ? p / pow_t<T>(u[0], gamma) : T(INFINITY);
+  return ok ? p * rho_pow_neg(u[0], gamma) : T(INFINITY);
 }
 
 template <class T>
@@ -96,6 +90,10 @@ __global__ void __launch_bounds__(KT<D, R>::THREADS) kxrcf_kernel(GridArgs a, co
   using G = Geo<D, R>;
   constexpr int NV = G::NV, N0 = G::N0, NT = G::NT, F = G::F, SN = K::SN, TH = K::THREADS;
   constexpr int EX = max_ext<D, R>();
+  // both faces of a direction in one pass over the stencil while their accumulators fit in ~80
+  // registers (not for d = 3, R = 3: 2 x 9 points x 5 variables), and full unrolling up to 33 cells
+  constexpr int SP = (2 * NT * NV * sizeof(T) <= 320) ? 2 : 1;
+  constexpr int UL = N0 <= 33 ? N0 : 4;
   extern __shared__ unsigned char kx_smem[];
   T* sm = reinterpret_cast<T*>(kx_smem);  // [NV][SN] cell averages
   T* ws = sm + NV * SN;                    // [F][N0] r_0 face rows
@@ -152,30 +150,40 @@ __global__ void __launch_bounds__(KT<D, R>::THREADS) kxrcf_kernel(GridArgs a, co
         }
       const int c = (loc[0] + K::H) + K::SX * ((loc[1] + K::H) + K::SY * (D == 3 ? loc[2] + K::H : 0));
 #pragma unroll 1
-      for (int side = 0; side < 2; ++side) {
+      for (int s0 = 0; s0 < 2; s0 += SP) {
         // the ring cell before the tile needs its high face only, the one after it its low face
-        if ((ld < 0 && side == 0) || (ld >= td && side == 1)) continue;
-        T acc[NT][NV];
+        // (the other face of a ring cell is computed when SP = 2 but not stored)
+        if (SP == 1 && ((ld < 0 && s0 == 0) || (ld >= td && s0 == 1))) continue;
+        T acc[SP][NT][NV];
 #pragma unroll
-        for (int t = 0; t < NT; ++t)
+        for (int si = 0; si < SP; ++si)
 #pragma unroll
-          for (int v = 0; v < NV; ++v) acc[t][v] = T(0);
-        const T* wrow = ws + ((dir * 2 + side) * NT) * N0;
-#pragma unroll 4
+          for (int t = 0; t < NT; ++t)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[si][t][v] = T(0);
+        const T* wrow = ws + ((dir * 2 + s0) * NT) * N0;
+#pragma unroll UL
         for (int l = 0; l < N0; ++l) {
           const int o = c + c_delta<D, R>[l];
           T g[NV];
 #pragma unroll
           for (int v = 0; v < NV; ++v) g[v] = sm[v * SN + o];
 #pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            const T w = wrow[t * N0 + l];
+          for (int si = 0; si < SP; ++si)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[t][v] = fma(w, g[v], acc[t][v]);
-          }
+            for (int t = 0; t < NT; ++t) {
+              const T w = wrow[(si * NT + t) * N0 + l];
+#pragma unroll
+              for (int v = 0; v < NV; ++v) acc[si][t][v] = fma(w, g[v], acc[si][t][v]);
+            }
         }
 #pragma unroll
-        for (int t = 0; t < NT; ++t) qb[(side * NT + t) * EX + e] = entropy<D, T>(acc[t], gamma);
+        for (int si = 0; si < SP; ++si) {
+          const int side = s0 + si;
+          if ((ld < 0 && side == 0) || (ld >= td && side == 1)) continue;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) qb[(side * NT + t) * EX + e] = entropy<D, T>(acc[si][t], gamma);
+        }
       }
     }
     __syncthreads();

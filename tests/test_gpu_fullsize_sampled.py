@@ -80,3 +80,44 @@ def test_full_size_rhs_matches_oracle_on_sampled_cells(kfvm, name):
         got = L[(slice(None),) + cell].cpu().numpy()
         worst = max(worst, float(np.abs(got - Lr[centre]).max()))
     assert worst <= tol, (worst, tol)
+
+
+@pytest.mark.parametrize("name", ["voronoi2d-1024", "halfsine3d-256"])
+def test_full_size_kxrcf_matches_oracle_on_sampled_cells(kfvm, name):
+    """The KXRCF path as bench.py times it (FP32, "recon" 4) at full size.  At each sampled cell: the
+    indicator's decision against the oracle's ratio on the crop (the indicator of a cell reads the cells
+    within R + 1, all inside the crop; either decision is accepted within 2e-4 of Delta^m, the FP32 band
+    of test_gpu_kxrcf.py), and L(U) against the oracle's gated L on the GPU's mask (2e-5 max|U| / h)."""
+    W = bench._workloads()[name]
+    U0 = W.make("cuda").contiguous()
+    g = kfvm.KFVM(list(W.n), dims=W.dims, radius=W.R, bc=W.bc)
+    g.set_option("precision", 32)
+    g.set_option("recon", 4)
+    mask = g.kxrcf_mask(U0).cpu().numpy()
+    L = g.rhs(U0)
+    g.sync_status()
+    assert (mask == 0).any() and (mask == 1).any()
+    half = W.R + 1
+    shape = tuple(U0.shape[1:])
+    h = 1.0 / W.n[0]
+    thresh = h ** 1.5
+    scale = float(U0.abs().max().item())
+    tol = 2e-5 * scale / h
+    worst, decided = 0.0, 0
+    for cell in _sample_cells(shape, half, seed=sum(map(ord, name)) + 1):
+        sl = tuple(slice(c - half, c + half + 1) for c in cell)
+        crop = np.ascontiguousarray(U0[(slice(None),) + sl].cpu().numpy())
+        n_crop = [2 * half + 1] * W.dims
+        box = dict(lo=[0.0] * W.dims, hi=[(2 * half + 1) * h] * W.dims)
+        centre = tuple([half] * W.dims)
+        ratio, _ = oracle.Oracle(n_crop, dim=W.dims, R=W.R, bc="outflow", **box).kxrcf(crop)
+        if abs(ratio[centre] - thresh) > 2e-4:
+            assert mask[cell] == (1 if ratio[centre] < thresh else 0), (cell, ratio[centre], thresh)
+            decided += 1
+        ref = oracle.Oracle(n_crop, dim=W.dims, R=W.R, bc="outflow", recon="gated",
+                            mask=np.ascontiguousarray(mask[sl]).ravel(), **box)
+        Lr = ref.rhs(crop)
+        got = L[(slice(None),) + cell].cpu().numpy()
+        worst = max(worst, float(np.abs(got - Lr[(slice(None),) + centre]).max()))
+    assert decided >= SAMPLES // 2
+    assert worst <= tol, (worst, tol)

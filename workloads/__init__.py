@@ -19,6 +19,9 @@ conserved variables rho, rho*u, rho*v[, rho*w], E, gamma = 1.4):
 * ``half_sine_voronoi_3d(n, k, seed)``  x < 1/2: rho = 1 + 0.2 sin(2 pi (x+y+z)),
                          u = v = w = 1, p = 1; x >= 1/2: k Voronoi regions with
                          sites uniform in [1/2,1] x [0,1]^2 and the constants above.
+* ``isentropic_vortex(n, R, t)``  the isentropic vortex of Sec. 6.1 on the
+                         periodic square [-10, 10]^2, advected by (1, 1): an
+                         exact smooth solution of the Euler equations.
 * ``mixed_voronoi(dim, n, k, seed)``  k regions over the whole box; per region a
                          coin (probability 1/2) picks the smooth sine state, else a
                          random constant state as above.
@@ -130,6 +133,27 @@ def sine_3d_exact_density(n: int, t: float) -> np.ndarray:
     Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
     damp = (math.sin(math.pi * h) / (math.pi * h)) ** 3
     return 1.0 + 0.2 * np.sin(2 * math.pi * (X + Y + Z - 3 * t)) * damp
+
+
+def _vortex_prim(coords, t, gamma=GAMMA):
+    """Isentropic vortex of radius 1 on [-10, 10]^2 (Sec. 6.1), advected by (1, 1) for a time t:
+    omega = 5 sqrt(2e)/(4 pi) exp(-r^2/2) about the centre (t, t) (periodic images are below 1e-21),
+    rho = (1 + (1-gamma)/2 omega^2)^(1/(gamma-1)), u = 1 - y omega, v = 1 + x omega,
+    p = (1/gamma) (1 + (1-gamma)/2 omega^2)^(gamma/(gamma-1))."""
+    x = torch.remainder(coords[0] - t + 10.0, 20.0) - 10.0
+    y = torch.remainder(coords[1] - t + 10.0, 20.0) - 10.0
+    om = 5.0 * math.sqrt(2.0 * math.e) / (4.0 * math.pi) * torch.exp(-0.5 * (x * x + y * y))
+    base = 1.0 + 0.5 * (1.0 - gamma) * om * om
+    rho = base ** (1.0 / (gamma - 1.0))
+    p = base ** (gamma / (gamma - 1.0)) / gamma
+    return rho, [1.0 - y * om, 1.0 + x * om], p
+
+
+def isentropic_vortex(n: int, R: int = 2, t: float = 0.0, device="cpu") -> torch.Tensor:
+    """The isentropic vortex (Sec. 6.1) on the periodic square [-10, 10]^2 with n x n cells; at
+    t > 0 the exact solution (the initial state translated by (t, t)); t = 20 is the initial state."""
+    h = 20.0 / n
+    return _cell_average(lambda c: _vortex_prim(c, t), 2, [n, n], [-10.0, -10.0], [h, h], R, device)
 
 
 def _draw_regions(rng: SplitMix64, k: int, dim: int, site_lo, site_hi, with_coin: bool):
