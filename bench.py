@@ -210,6 +210,13 @@ def algo_flops_per_cell(dims, R, mode):
     return 2 * nv * (sum(n * (F + M) for n in sizes) + nq * M + nq * F)
 
 
+def gate_flops_per_cell(dims):
+    """Algorithmic flops of the learned gate per cell (FMA = 2): in -> 32 -> 32 -> 1 with in = 26 (2D) or
+    68 (3D) inputs; it runs on the tensor pipe (mma.sync BF16, FP32 accumulation), not the FP32 pipe."""
+    n_in = 26 if dims == 2 else 68
+    return 2 * (n_in * 32 + 32 * 32 + 32)
+
+
 def flush_l2(buf):
     buf.zero_()
 
@@ -462,6 +469,10 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak_flops if peak_flops else None, "traffic": traffic,
                 "peak_source": f"measured live: FP{64 if path == 'fp64' else 32} FMA loop on every SM",
                 "algo_flops_per_cell": flops / ncell, "mode": mode, "gated_smooth_fraction": smooth_frac,
+                # the learned gate's own work, on the tensor pipe (not in "achieved", which is FP32-pipe work)
+                "gate_tensor_flops_per_cell": gate_flops_per_cell(W.dims) if path == "gated" else None,
+                "achieved_incl_gate_tflops": ((flops + gate_flops_per_cell(W.dims) * ncell) * 3 * args.steps
+                                              / (kms * 1e-3) / 1e12) if (path == "gated" and kms > 0) else None,
                 "launches_per_stage": launches_per_stage,
                 "kernel_share": {k: round(v[1] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
 

@@ -13,12 +13,14 @@
 // (rho <= 0, p <= 0 or not finite) on either side of a point, or such a cell
 // average, flags the cell.
 //
-// One thread per cell of a TX x TY x TZ tile whose cell averages (halo R + 1,
-// through the ghost-cell map) sit in shared memory.  The directions are taken
-// one at a time: the tile's cells and the ring of cells just outside it along
-// that direction reconstruct their faces normal to it (the ring only the face
-// it shares with the tile) and park q at those points in shared memory; then
-// every tile cell compares its two faces with its neighbours'.  Each face
+// A CTA owns a TX x TY x TZ tile whose cell averages (halo R + 1, through the
+// ghost-cell map) sit in shared memory.  The directions are taken one at a
+// time: the tile's cells and the ring of cells just outside it along that
+// direction (one thread each: the block has as many threads as the largest such
+// set, so the ring is no second wave) reconstruct their faces normal to it (the
+// ring only the face it shares with the tile) and park q at those points in
+// shared memory, numbered with x fastest so that a warp reads consecutive
+// cells; then every tile cell compares its two faces with its neighbours'.  Each face
 // state is computed once per direction instead of once per side.  T = double
 // reads the float64 state (FP64 mode); T = float reads its float32 shadow (FP32
 // mode), so the decision is taken in the precision of the path it serves.
@@ -53,6 +55,11 @@ __host__ __device__ constexpr int ext_count(int dir) {
   using K = KT<D, R>;
   return K::THREADS / K::tdim(dir) * (K::tdim(dir) + 2);
 }
+// extent of axis k in the ring-extended numbering of direction dir
+template <int D, int R>
+__host__ __device__ constexpr int ext_dim(int dir, int k) {
+  return KT<D, R>::tdim(k) + (k == dir ? 2 : 0);
+}
 
 template <int D, int R>
 __host__ __device__ constexpr int max_ext() {
@@ -83,13 +90,13 @@ __device__ __forceinline__ T jump(T a, T b) {
 }
 
 template <int D, int R, class T>
-__global__ void __launch_bounds__(KT<D, R>::THREADS) kxrcf_kernel(GridArgs a, const T* __restrict__ U,
+__global__ void __launch_bounds__(max_ext<D, R>()) kxrcf_kernel(GridArgs a, const T* __restrict__ U,
                                                                    const double* __restrict__ w64, T thresh,
                                                                    unsigned char* __restrict__ mask) {
   using K = KT<D, R>;
   using G = Geo<D, R>;
-  constexpr int NV = G::NV, N0 = G::N0, NT = G::NT, F = G::F, SN = K::SN, TH = K::THREADS;
-  constexpr int EX = max_ext<D, R>();
+  constexpr int NV = G::NV, N0 = G::N0, NT = G::NT, F = G::F, SN = K::SN;
+  constexpr int EX = max_ext<D, R>(), TH = EX;  // threads = the largest tile + ring set
   // both faces of a direction in one pass over the stencil while their accumulators fit in ~80
   // registers (not for d = 3, R = 3: 2 x 9 points x 5 variables), and full unrolling up to 33 cells
   constexpr int SP = (2 * NT * NV * sizeof(T) <= 320) ? 2 : 1;
@@ -125,29 +132,23 @@ __global__ void __launch_bounds__(KT<D, R>::THREADS) kxrcf_kernel(GridArgs a, co
   // this thread's tile cell
   const int lx = tid % K::TX, ly = (tid / K::TX) % K::TY, lz = tid / (K::TX * K::TY);
   const int me[3] = {lx, ly, lz};
-  const bool active = org[0] + lx < a.n[0] && org[1] + ly < a.n[1] && (D == 2 || org[2] + lz < a.n[2]);
+  const bool active = tid < K::THREADS && org[0] + lx < a.n[0] && org[1] + ly < a.n[1] &&
+                      (D == 2 || org[2] + lz < a.n[2]);
   const int c_me = (lx + K::H) + K::SX * ((ly + K::H) + K::SY * (D == 3 ? lz + K::H : 0));
   T jmax = T(0);
 
 #pragma unroll 1
   for (int dir = 0; dir < D; ++dir) {
     const int td = K::tdim(dir);
-    const int E = K::THREADS / td * (td + 2);
+    const int e0 = ext_dim<D, R>(dir, 0), e1 = ext_dim<D, R>(dir, 1);
+    const int E = e0 * e1 * ext_dim<D, R>(dir, 2);
     // phase 1: q at the faces normal to dir of the tile cells and the ring along dir
-#pragma unroll 1
-    for (int e = tid; e < E; e += TH) {
-      // e -> (position along dir in -1..td, the other coordinates in the tile)
-      const int ld = e % (td + 2) - 1;
-      int rest = e / (td + 2);
-      int loc[3];
-      loc[dir] = ld;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (k != dir) {
-          const int tk = K::tdim(k);
-          loc[k] = rest % tk;
-          rest /= tk;
-        }
+    if (tid < E) {
+      const int e = tid;
+      // e -> (x, y, z) with x fastest; the coordinate along dir runs over -1..td
+      int loc[3] = {e % e0, (e / e0) % e1, e / (e0 * e1)};
+      loc[dir] -= 1;
+      const int ld = loc[dir];
       const int c = (loc[0] + K::H) + K::SX * ((loc[1] + K::H) + K::SY * (D == 3 ? loc[2] + K::H : 0));
 #pragma unroll 1
       for (int s0 = 0; s0 < 2; s0 += SP) {
@@ -189,22 +190,15 @@ __global__ void __launch_bounds__(KT<D, R>::THREADS) kxrcf_kernel(GridArgs a, co
     __syncthreads();
     // phase 2: jumps across this thread's two faces normal to dir
     if (active) {
-      int loc[3] = {me[0], me[1], me[2]};
-      const int ld = loc[dir];
-      // index of (ld + k) along dir in the ring-extended numbering of phase 1
-      int rest_idx = 0, mul = 1;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (k != dir) {
-          rest_idx += loc[k] * mul;
-          mul *= K::tdim(k);
-        }
-      const int e_me = rest_idx * (td + 2) + (ld + 1);
+      const int ld = me[dir];
+      // this cell and its neighbours along dir in the ring-extended numbering of phase 1
+      const int e_me = (me[0] + (dir == 0)) + e0 * ((me[1] + (dir == 1)) + e1 * (me[2] + (dir == 2)));
+      const int stride = dir == 0 ? 1 : (dir == 1 ? e0 : e0 * e1);
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         const int g_nb = org[dir] + ld + (side ? 1 : -1);
         if ((g_nb < 0 || g_nb >= a.n[dir]) && a.bc[dir][side] != KFVM_BC_PERIODIC) continue;
-        const int e_nb = e_me + (side ? 1 : -1);
+        const int e_nb = e_me + (side ? stride : -stride);
 #pragma unroll
         for (int t = 0; t < NT; ++t)
           jmax = fmax(jmax, jump(qb[(side * NT + t) * EX + e_me], qb[((1 - side) * NT + t) * EX + e_nb]));
@@ -249,7 +243,7 @@ cudaError_t launch_dr(kfvm_ctx* ctx, const T* U, unsigned char* mask, cudaStream
   auto kern = kxrcf_kernel<D, R, T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<tiles, K::THREADS, smem, st>>>(a, U, ctx->d_w64, thresh, mask);
+  kern<<<tiles, max_ext<D, R>(), smem, st>>>(a, U, ctx->d_w64, thresh, mask);
   ctx->launches += 1;
   return cudaGetLastError();
 }

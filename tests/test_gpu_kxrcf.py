@@ -4,10 +4,11 @@ Every call goes through the C ABI.  The indicator's decision compares a float ra
 Delta^m, so near the threshold both sides can disagree by rounding; cells whose oracle ratio
 lies within a band around Delta^m accept either decision and every other cell must match
 exactly.  FP64 band: 1e-9 relative (the two sides' reconstructions differ by ~1e-15).  FP32
-band: 2e-4 absolute on the ratio, from the float32 arithmetic: the float32 copy of the state
-and a contraction whose weights sum in absolute value to ~3 give states within a few 1e-7
-relative; the pressure recovery E - |m|^2/(2 rho) amplifies that by E/p (<= ~10 on these
-inputs), so q and its jumps carry errors of ~1e-5 of <Q>, and the band keeps a 20x margin.
+band: 1e-5 absolute on the ratio, from the float32 arithmetic: the float32 copy of the state
+(6e-8 relative) and a contraction whose weights sum in absolute value to ~3 give states within
+~2e-7 relative; the pressure recovery E - |m|^2/(2 rho) amplifies that by E/p (<= ~13 on these
+inputs) and rho^-gamma adds ~2e-7, so each q carries ~2e-6 of <Q> and a jump ~4e-6: the band
+keeps a 2.5x margin.  (Delta^m itself is 3e-5 at 1024^2, so the band must stay well below it.)
 """
 import numpy as np
 import pytest
@@ -19,6 +20,7 @@ import oracle  # noqa: E402
 import workloads  # noqa: E402
 
 G = 1.4
+FP32_BAND = 1e-5  # absolute, on the ratio (see above)
 
 
 @pytest.fixture(scope="module")
@@ -56,7 +58,7 @@ def test_mask_matches_oracle(kfvm, dim, R, n, bc, seed, precision):
     g.set_option("precision", precision)
     got = g.kxrcf_mask(U0.cuda()).cpu().numpy()
     th = _thresh(n)
-    band = np.abs(ratio - th) <= (1e-9 * th if precision == 64 else 2e-4)
+    band = np.abs(ratio - th) <= (1e-9 * th if precision == 64 else FP32_BAND)
     assert (got[~band] == want[~band]).all(), np.argwhere((got != want) & ~band)[:5]
     assert set(np.unique(got)) <= {0, 1}
     assert (want == 0).any() and (want == 1).any()
