@@ -30,7 +30,8 @@ import numpy as np
 from . import gate, stencils
 from .build import build as _build
 
-__all__ = ["Oracle", "weights", "flat_weights", "stencils", "phi_matrices", "riemann_flux", "face_points", "gate"]
+__all__ = ["Oracle", "weights", "flat_weights", "stencils", "phi_matrices", "char_matrices", "riemann_flux",
+           "face_points", "gate"]
 
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -54,6 +55,7 @@ class _Problem(ctypes.Structure):
         ("positivity", _I), ("kappa", _D), ("eta", _D),
         ("mask", ctypes.POINTER(ctypes.c_ubyte)),
         ("kxrcf_m", _D),
+        ("vars", _I),
     ]
 
 
@@ -87,6 +89,8 @@ def lib():
         L.kfo_step.restype = _I
         L.kfo_phi.argtypes = [_I, _D, _PD, _PD, _PD]
         L.kfo_phi.restype = None
+        L.kfo_char.argtypes = [_I, _D, _PD, _I, _PD, _PD]
+        L.kfo_char.restype = None
         L.kfo_riemann.argtypes = [_I, _D, _I, _I, _PD, _PD, _PD]
         L.kfo_riemann.restype = _I
         _lib = L
@@ -156,6 +160,16 @@ def phi_matrices(dim: int, gamma: float, ut):
     return phi, phinv
 
 
+def char_matrices(dim: int, gamma: float, ut, dir: int):
+    """(L, R) of the characteristic variables of direction dir at reference state ut (Sec. 3.4.1)."""
+    nv = dim + 2
+    ut = np.ascontiguousarray(np.asarray(ut, dtype=np.float64))
+    L = np.zeros((nv, nv))
+    R = np.zeros((nv, nv))
+    lib().kfo_char(dim, float(gamma), _pd(ut), int(dir), _pd(L), _pd(R))
+    return L, R
+
+
 def riemann_flux(dim: int, gamma: float, dir: int, uL, uR, solver: str = "hllc") -> np.ndarray:
     nv = dim + 2
     uL = np.ascontiguousarray(np.asarray(uL, dtype=np.float64))
@@ -178,7 +192,7 @@ class Oracle:
     def __init__(self, n, dim: int = 2, R: int = 2, lo=None, hi=None, bc="periodic", gamma: float = 1.4,
                  ell: float = 5.0, eps: float = 1e-40, recon: str = "weno", riemann: str = "hllc",
                  positivity: bool = True, kappa: float = 0.1, eta: float = 0.0, mask=None,
-                 kxrcf_m: float = 1.5):
+                 kxrcf_m: float = 1.5, variables: str = "linprim"):
         self.dim, self.R, self.nv = dim, R, dim + 2
         n = list(n) + [1] * (3 - len(n))
         lo = list(lo) if lo is not None else [0.0] * dim
@@ -218,6 +232,7 @@ class Oracle:
         pb.wts, pb.gl_w = _pd(self._wts), _pd(self._gl)
         pb.recon = {"weno": 0, "linear": 1, "gated": 2, "kxrcf": 3}[recon]
         pb.kxrcf_m = float(kxrcf_m)
+        pb.vars = {"linprim": 0, "characteristic": 1}[variables]
         if mask is not None:
             self._mask = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).ravel())
             if self._mask.size != self.ncell:

@@ -28,6 +28,11 @@
  *                    normalised (Eqs. 24-25), WENO-AO blend (Eq. 19), back
  *                    transform (Eq. 28).  Mode 1 is the unlimited linear S0
  *                    reconstruction of the conservative variables.
+ *   kfo_char         Sec. 3.4.1: characteristic variables of one direction,
+ *                    Phi = L and Phi^{-1} = R from the eigenvectors of the
+ *                    flux Jacobian at the central cell average; with them
+ *                    the WENO-AO weights are computed once per direction and
+ *                    serve only that direction's faces.
  *   kfo_kxrcf        Sec. 3.5 and Sec. 5.3 step 2 items 1-2: the KXRCF
  *                    troubled-cell indicator on the unlimited linear states,
  *                    which decides per cell between the linear and the WENO-AO
@@ -305,6 +310,7 @@ typedef struct {
   double kappa, eta;    /* bound relaxation kappa and flattener eta of Sec. 4.1 */
   const unsigned char* mask; /* recon 2: per cell, 1 = linear (smooth), 0 = WENO-AO */
   double kxrcf_m;       /* recon 3: power m of the KXRCF threshold Delta^m (Sec. 3.5: m = 3/2) */
+  int vars;             /* WENO-AO variables: 0 linearized primitive (Sec. 3.4.2), 1 characteristic (Sec. 3.4.1) */
 } kfo_problem;
 
 static long ncell_of(const kfo_problem* pb) { return (long)pb->n[0] * pb->n[1] * pb->n[2]; }
@@ -357,6 +363,61 @@ void kfo_phi(int dim, double gamma, const double* ut, double* phi, double* phinv
   phinv[(nv - 1) * nv + nv - 1] = 1.0 / (gamma - 1.0);
 }
 
+/* Characteristic variables of direction dir at the reference state ut (Sec. 3.4.1): the flux
+   Jacobian A = dF_dir/dU = R Lambda L, Phi = L (rows: left eigenvectors) and Phi^{-1} = R
+   (columns: right eigenvectors), L R = I.  Waves in the order u_n - c, entropy, the shear waves of
+   the tangential axes in increasing order, u_n + c.  With b1 = (gamma-1)/c^2, b2 = b1 |u|^2/2,
+   H = (E + p)/rho and n the unit normal:
+     R: (1, u - c n, H - c u_n), (1, u, |u|^2/2), (0, e_a, u_a), (1, u + c n, H + c u_n);
+     L: (b2 + u_n/c, -b1 u - n/c, b1)/2, (1 - b2, b1 u, -b1), (-u_a, e_a, 0), (b2 - u_n/c, -b1 u + n/c, b1)/2. */
+void kfo_char(int dim, double gamma, const double* ut, int dir, double* L, double* Rm) {
+  const int nv = dim + 2;
+  const double rho = ut[0];
+  double u[3] = {0, 0, 0}, q2 = 0;
+  for (int k = 0; k < dim; ++k) { u[k] = ut[1 + k] / rho; q2 += u[k] * u[k]; }
+  const double p = (gamma - 1.0) * (ut[nv - 1] - 0.5 * rho * q2);
+  const double c = sqrt(gamma * p / rho), H = (ut[nv - 1] + p) / rho;
+  const double b1 = (gamma - 1.0) / (c * c), b2 = 0.5 * b1 * q2, un = u[dir];
+  memset(L, 0, sizeof(double) * nv * nv);
+  memset(Rm, 0, sizeof(double) * nv * nv);
+  /* columns of R */
+  Rm[0 * nv + 0] = 1.0;
+  Rm[0 * nv + 1] = 1.0;
+  Rm[0 * nv + nv - 1] = 1.0;
+  for (int k = 0; k < dim; ++k) {
+    const double nk = (k == dir) ? 1.0 : 0.0;
+    Rm[(1 + k) * nv + 0] = u[k] - c * nk;
+    Rm[(1 + k) * nv + 1] = u[k];
+    Rm[(1 + k) * nv + nv - 1] = u[k] + c * nk;
+  }
+  Rm[(nv - 1) * nv + 0] = H - c * un;
+  Rm[(nv - 1) * nv + 1] = 0.5 * q2;
+  Rm[(nv - 1) * nv + nv - 1] = H + c * un;
+  /* rows of L */
+  L[0 * nv + 0] = 0.5 * (b2 + un / c);
+  L[1 * nv + 0] = 1.0 - b2;
+  L[(nv - 1) * nv + 0] = 0.5 * (b2 - un / c);
+  for (int k = 0; k < dim; ++k) {
+    const double nk = (k == dir) ? 1.0 : 0.0;
+    L[0 * nv + 1 + k] = 0.5 * (-b1 * u[k] - nk / c);
+    L[1 * nv + 1 + k] = b1 * u[k];
+    L[(nv - 1) * nv + 1 + k] = 0.5 * (-b1 * u[k] + nk / c);
+  }
+  L[0 * nv + nv - 1] = 0.5 * b1;
+  L[1 * nv + nv - 1] = -b1;
+  L[(nv - 1) * nv + nv - 1] = 0.5 * b1;
+  /* shear waves: one per tangential axis a, in increasing order */
+  int w = 2;
+  for (int a = 0; a < dim; ++a) {
+    if (a == dir) continue;
+    Rm[(1 + a) * nv + w] = 1.0;
+    Rm[(nv - 1) * nv + w] = u[a];
+    L[w * nv + 0] = -u[a];
+    L[w * nv + 1 + a] = 1.0;
+    ++w;
+  }
+}
+
 /* offset of the weights of stencil q inside pb->wts */
 static long wts_offset(const kfo_problem* pb, int q) {
   long off = 0;
@@ -374,7 +435,8 @@ static long sub_start(const kfo_problem* pb, int q) {
  * Riemann states of every cell (Sec. 5.3 step 2).
  *   U     : [nv][ncell]
  *   faces : out, [F][nv][ncell]
- *   omega : optional out, [nq][nv][ncell] normalised nonlinear weights (WENO mode)
+ *   omega : optional out, [nq][nv][ncell] normalised nonlinear weights (WENO mode, linearized
+ *           primitive variables)
  */
 int kfo_kxrcf(const kfo_problem* pb, const double* U, double* ratio, unsigned char* mask);
 
@@ -422,60 +484,70 @@ int kfo_reconstruct(const kfo_problem* pb, const double* U, double* faces, doubl
               ws[s * nv + v] = acc;
             }
         } else {
-          /* Phi from the central cell average (the l with offset 0) */
+          /* the reference state: the central cell average (the l with offset 0) */
           int lc = -1;
           for (int l = 0; l < n0; ++l)
             if (pb->offs[3 * l] == 0 && pb->offs[3 * l + 1] == 0 && pb->offs[3 * l + 2] == 0) lc = l;
-          double phi[25], phinv[25];
-          kfo_phi(dim, pb->gamma, sten + lc * nv, phi, phinv);
-          /* W_h = Phi U_h over the whole stencil (Eq. 33) */
-          for (int v = 0; v < nv; ++v)
-            for (int l = 0; l < n0; ++l) {
-              double acc = 0;
-              for (int j = 0; j < nv; ++j) acc += phi[v * nv + j] * sten[l * nv + j];
-              W[v * n0 + l] = acc;
-            }
-          for (int v = 0; v < nv; ++v) {
-            double beta[8], om[8];
-            for (int q = 0; q < nq; ++q) {
-              const int nl = pb->sub_len[q];
-              const int* idx = pb->sub_idx + sub_start(pb, q);
-              const double* rf = pb->wts + wts_offset(pb, q);
-              const double* rd = rf + (long)F * nl;
-              for (int s = 0; s < F; ++s) {
+          /* linearized primitive variables: one Phi for every face (Sec. 3.4.2); characteristic
+             variables: one Phi per direction, serving that direction's faces only (Sec. 3.4.1) */
+          const int npass = pb->vars == 1 ? dim : 1;
+          const int nt = F / (2 * dim);
+          for (int pass = 0; pass < npass; ++pass) {
+            double phi[25], phinv[25];
+            if (pb->vars == 1)
+              kfo_char(dim, pb->gamma, sten + lc * nv, pass, phi, phinv);
+            else
+              kfo_phi(dim, pb->gamma, sten + lc * nv, phi, phinv);
+            const int s_lo = pb->vars == 1 ? 2 * pass * nt : 0, s_hi = pb->vars == 1 ? (2 * pass + 2) * nt : F;
+            /* W_h = Phi U_h over the whole stencil (Eq. 33, or L U_h) */
+            for (int v = 0; v < nv; ++v)
+              for (int l = 0; l < n0; ++l) {
                 double acc = 0;
-                for (int l = 0; l < nl; ++l) acc += rf[s * nl + l] * W[v * n0 + idx[l]];
-                vals[q * F + s] = acc;
+                for (int j = 0; j < nv; ++j) acc += phi[v * nv + j] * sten[l * nv + j];
+                W[v * n0 + l] = acc;
               }
-              double b = 0;
-              for (int m = 0; m < M; ++m) {
-                double acc = 0;
-                for (int l = 0; l < nl; ++l) acc += rd[m * nl + l] * W[v * n0 + idx[l]];
-                b += acc * acc;
-              }
-              beta[q] = b;
-            }
-            double sum = 0;
-            for (int q = 0; q < nq; ++q) { om[q] = pb->lin_w[q] / (beta[q] * beta[q] + pb->eps); sum += om[q]; }
-            for (int q = 0; q < nq; ++q) om[q] /= sum;
-            if (omega)
-              for (int q = 0; q < nq; ++q) omega[((long)q * nv + v) * nc + c] = om[q];
-            const double g0 = pb->lin_w[0];
-            for (int s = 0; s < F; ++s) {
-              double acc = om[0] / g0 * vals[s];
-              for (int q = 1; q < nq; ++q) acc += (om[q] - om[0] * pb->lin_w[q] / g0) * vals[q * F + s];
-              ws[s * nv + v] = acc;
-            }
-          }
-          /* back to conservative variables, u_s = Phi^{-1} w_s */
-          for (int s = 0; s < F; ++s) {
-            double u[5];
             for (int v = 0; v < nv; ++v) {
-              double acc = 0;
-              for (int j = 0; j < nv; ++j) acc += phinv[v * nv + j] * ws[s * nv + j];
-              u[v] = acc;
+              double beta[8], om[8];
+              for (int q = 0; q < nq; ++q) {
+                const int nl = pb->sub_len[q];
+                const int* idx = pb->sub_idx + sub_start(pb, q);
+                const double* rf = pb->wts + wts_offset(pb, q);
+                const double* rd = rf + (long)F * nl;
+                for (int s = s_lo; s < s_hi; ++s) {
+                  double acc = 0;
+                  for (int l = 0; l < nl; ++l) acc += rf[s * nl + l] * W[v * n0 + idx[l]];
+                  vals[q * F + s] = acc;
+                }
+                double b = 0;
+                for (int m = 0; m < M; ++m) {
+                  double acc = 0;
+                  for (int l = 0; l < nl; ++l) acc += rd[m * nl + l] * W[v * n0 + idx[l]];
+                  b += acc * acc;
+                }
+                beta[q] = b;
+              }
+              double sum = 0;
+              for (int q = 0; q < nq; ++q) { om[q] = pb->lin_w[q] / (beta[q] * beta[q] + pb->eps); sum += om[q]; }
+              for (int q = 0; q < nq; ++q) om[q] /= sum;
+              if (omega && pb->vars == 0)
+                for (int q = 0; q < nq; ++q) omega[((long)q * nv + v) * nc + c] = om[q];
+              const double g0 = pb->lin_w[0];
+              for (int s = s_lo; s < s_hi; ++s) {
+                double acc = om[0] / g0 * vals[s];
+                for (int q = 1; q < nq; ++q) acc += (om[q] - om[0] * pb->lin_w[q] / g0) * vals[q * F + s];
+                ws[s * nv + v] = acc;
+              }
             }
-            for (int v = 0; v < nv; ++v) ws[s * nv + v] = u[v];
+            /* back to conservative variables, u_s = Phi^{-1} w_s */
+            for (int s = s_lo; s < s_hi; ++s) {
+              double u[5];
+              for (int v = 0; v < nv; ++v) {
+                double acc = 0;
+                for (int j = 0; j < nv; ++j) acc += phinv[v * nv + j] * ws[s * nv + j];
+                u[v] = acc;
+              }
+              for (int v = 0; v < nv; ++v) ws[s * nv + v] = u[v];
+            }
           }
         }
         for (int s = 0; s < F; ++s) {
