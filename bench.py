@@ -101,7 +101,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--path", choices=["auto", "fp64", "fp32", "gated", "kxrcf"], default="auto")
+    ap.add_argument("--path", choices=["auto", "fp64", "fp64char", "fp32", "gated", "kxrcf"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline path only (no other paths, e2e or CPU baseline): for profiler runs")
@@ -246,6 +246,8 @@ def make_solver(W, path, n=None):
         g.set_option("precision", 32)
     if path == "kxrcf":  # the paper's troubled-cell indicator (Sec. 3.5) instead of the learned gate
         g.set_option("recon", 4)
+    if path == "fp64char":  # plain FP64 WENO-AO in characteristic variables (Sec. 3.4.1)
+        g.set_option("variables", 1)
     if path == "gated":
         g.gate_set_params(np.load(W.gate_path()))
         g.set_option("gate_threshold", GATE_THRESHOLD)
@@ -389,18 +391,20 @@ def main():
 
     # ---- the other paths on the same workload (plain FP64 is the metric's reference) ----
     others = {}
-    for other in ("fp64", "fp32", "gated", "kxrcf"):
+    for other in ("fp64", "fp64char", "fp32", "gated", "kxrcf"):
         if args.headline_only or other == path or (other == "gated" and not W.has_gate()):
             continue
+        if other == "fp64char" and W.fp64_planes:
+            continue  # radius 3 in float64 on 512^2 x 16 cells: ~25 s per step with three sets of weights
         k = max(3, args.steps // 4)
         Uo0, n_o, note = U0, None, None
-        if other == "fp64" and W.fp64_planes:
+        if other in ("fp64", "fp64char") and W.fp64_planes:
             # the plain FP64 path on the first z-planes of the same state (seconds per stage at full size)
             Uo0 = U0[:, :W.fp64_planes].contiguous()
             n_o = W.n[:2] + [W.fp64_planes]
             note = f"first {W.fp64_planes} z-planes of the state ({W.n[0]}x{W.n[1]}x{W.fp64_planes} cells)"
             k = 1
-        go, mso, _, _, _ = measure_path(W, other, Uo0, k, 1 if other == "fp64" else 2, stream, flush_buf, n_o,
+        go, mso, _, _, _ = measure_path(W, other, Uo0, k, 1 if other.startswith("fp64") else 2, stream, flush_buf, n_o,
                                         barrier=barrier)
         mso = job_time_ms(mso, dist, dev)
         cells = ncell if n_o is None else n_o[0] * n_o[1] * n_o[2]
@@ -438,9 +442,9 @@ def main():
            "l2": "flushed before every step, inside the timed region"}
 
     # ---- roofline of the dominant kernel ----
-    kern = "recon64" if path == "fp64" else "recon32"
+    kern = "recon64" if path.startswith("fp64") else "recon32"
     n_launch, kms = prof.get(kern, (0, 0.0))
-    mode = "weno" if path in ("fp64", "fp32") else "gated"
+    mode = "weno" if path in ("fp64", "fp64char", "fp32") else "gated"
     flops = algo_flops_per_cell(W.dims, W.R, "weno") * ncell
     smooth_frac = None
     if path in ("gated", "kxrcf"):
@@ -453,7 +457,7 @@ def main():
         smooth_frac = sum(fr) / len(fr)
         flops = ncell * (smooth_frac * algo_flops_per_cell(W.dims, W.R, "linear")
                          + (1 - smooth_frac) * algo_flops_per_cell(W.dims, W.R, "weno"))
-    peak_flops = pkg.measure_fma_peak(64 if path == "fp64" else 32)
+    peak_flops = pkg.measure_fma_peak(64 if path.startswith("fp64") else 32)
     # algorithmic flops of every timed stage over the kernel's summed device time (3D grids above the
     # Riemann-state buffer run as several launches per stage, one per z-slab)
     achieved = flops * 3 * args.steps / (kms * 1e-3) if kms > 0 else 0.0
@@ -467,7 +471,7 @@ def main():
     total_prof = sum(v[1] for v in prof.values())
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak_flops if peak_flops else None, "traffic": traffic,
-                "peak_source": f"measured live: FP{64 if path == 'fp64' else 32} FMA loop on every SM",
+                "peak_source": f"measured live: FP{64 if path.startswith('fp64') else 32} FMA loop on every SM",
                 "algo_flops_per_cell": flops / ncell, "mode": mode, "gated_smooth_fraction": smooth_frac,
                 # the learned gate's own work, on the tensor pipe (not in "achieved", which is FP32-pipe work)
                 "gate_tensor_flops_per_cell": gate_flops_per_cell(W.dims) if path == "gated" else None,
@@ -503,7 +507,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "gated": "f32+bf16", "kxrcf": "f32"}[path],
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp64char": "f64", "fp32": "f32", "gated": "f32+bf16", "kxrcf": "f32"}[path],
             "data": "synthetic",
             "config": {"workload": W.desc, "name": W.name, "grid": W.n, "radius": W.R, "path": path,
                        "gate": ({"params": f"paper_2401_16543_gb300/{W.gate}",

@@ -118,6 +118,14 @@ size_t kfvm_weights_count(const kfvm_ctx* ctx);
  *                 evaluated as in Sec. 5.3 step 2 items 1-2; kfvm_kxrcf_mask)
  *                 picks each cell's reconstruction from every stage's own
  *                 state, cells it does not flag take the linear one.
+ *   "variables"   WENO-AO variables: 0 linearized primitive (default,
+ *                 Sec. 3.4.2: one set of nonlinear weights per cell serves
+ *                 every face), 1 characteristic (Sec. 3.4.1: per direction,
+ *                 Phi = L and Phi^{-1} = R from the eigenvectors of that
+ *                 direction's flux Jacobian at the central cell average, and
+ *                 the weights recomputed per direction for its two faces).
+ *                 Characteristic variables run on the FP64 path only: in the
+ *                 FP32 mode the hot-path calls return KFVM_ERR_STATE.
  *   "riemann"     0 HLLC (default), 1 HLL; Batten wave speeds (Sec. 5.4).
  *   "positivity"  1 (default) apply the positivity-preserving limiter of
  *                 Sec. 4 to the Riemann states; 0 off.
@@ -151,12 +159,15 @@ kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double value);
 
 /* Riemann states at every face Gauss point of every cell (Sec. 5.3 steps 1-3):
  * ghost-cell map, linearized primitive transform (Eq. 33, appendix A with the
- * exact inverse), contraction with the weight tables, smoothness indicators
+ * exact inverse; or the characteristic transform of each direction, option
+ * "variables"), contraction with the weight tables, smoothness indicators
  * (Eq. 22), nonlinear weights (Eqs. 24-25), WENO-AO blend (Eq. 19), back
  * transform (Eq. 28), then the positivity limiter (Sec. 4) when enabled.
  * U: device, float64 state.  faces: device, F*nv*ncell values in the layout
- * and type described above.  Errors: KFVM_ERR_ARG, KFVM_ERR_STATE,
- * KFVM_ERR_CUDA (launch); non-admissible states raise the device flag. */
+ * and type described above.  Errors: KFVM_ERR_ARG, KFVM_ERR_STATE (weights
+ * not built, no network loaded in the gated mode, characteristic variables in
+ * the FP32 mode), KFVM_ERR_CUDA (launch); non-admissible states raise the
+ * device flag. */
 kfvm_status kfvm_reconstruct(kfvm_ctx* ctx, const double* U, void* faces, void* stream);
 
 /* Flux divergence from Riemann states (Sec. 5.3 steps 4-6): exterior states at

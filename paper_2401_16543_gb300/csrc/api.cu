@@ -186,6 +186,7 @@ kfvm_status check_ready(kfvm_ctx* ctx) {
   if (!ctx) return KFVM_ERR_ARG;
   if (!ctx->weights_built) return KFVM_ERR_STATE;
   if (ctx->recon == 2 && !ctx->gate_loaded) return KFVM_ERR_STATE;
+  if (ctx->vars == 1 && ctx->precision == 32) return KFVM_ERR_STATE;  // characteristic: FP64 kernels only
   return KFVM_OK;
 }
 
@@ -426,6 +427,9 @@ kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double v) {
   } else if (k == "profile") {
     if (v != 0 && v != 1) return KFVM_ERR_ARG;
     ctx->profile = (int)v;
+  } else if (k == "variables") {
+    if (v != 0 && v != 1) return KFVM_ERR_ARG;
+    ctx->vars = (int)v;
   } else if (k == "kxrcf_m") {
     if (!(v > 0 && v <= 16)) return KFVM_ERR_ARG;
     ctx->kxrcf_m = v;

@@ -18,6 +18,7 @@ struct GridArgs {
   double kappa, eta;
   int positivity;
   int riemann;
+  int vars;  // WENO-AO variables: 0 linearized primitive (Sec. 3.4.2), 1 characteristic (Sec. 3.4.1)
   int* status;
   DevScalars* scalars;
   // float32 copies for the mixed-precision kernels
@@ -44,6 +45,7 @@ inline GridArgs make_grid_args(const kfvm_ctx* c) {
   g.eta = c->eta;
   g.positivity = c->positivity;
   g.riemann = c->riemann;
+  g.vars = c->vars;
   g.status = c->d_status;
   g.scalars = c->d_scalars;
   g.gammaf = (float)c->gamma;

@@ -56,6 +56,7 @@ struct kfvm_ctx {
   int timeout_probe = 0;  // test hook: the next tensor-core launch waits on nothing and times out
   double kappa = 0.1, eta = 0.0, eps = 1e-40, gate_threshold = 0.5;
   double kxrcf_m = 1.5;  // power m of the KXRCF threshold Delta^m (recon mode 4)
+  int vars = 0;          // WENO-AO variables: 0 linearized primitive, 1 characteristic (FP64 path)
   // weights
   size_t wcount = 0;
   bool weights_built = false;

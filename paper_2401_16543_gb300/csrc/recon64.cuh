@@ -14,6 +14,9 @@
 //     (Eq. 28; energy row rho*u_i);
 //   * the positivity-preserving limiter of Sec. 4 (bounds from the 3^d
 //     neighbourhood, theta_rho, theta_p by 60 bisection steps).
+// With "variables" = 1 the WENO-AO cells reconstruct in characteristic
+// variables instead (Sec. 3.4.1, recon_cell_char): one set of nonlinear weights
+// per direction, serving that direction's faces.
 // In the linear mode the conservative variables are reconstructed with r_0.
 // The weight tables travel as a kernel parameter (constant bank, at most
 // 28 KB: d = 2, and d = 3 with R = 2) or are read from global memory
@@ -213,6 +216,150 @@ __device__ __forceinline__ void recon_cell(const GridArgs& a, const WF& W, const
   }
 }
 
+// Characteristic variables of direction dir at the reference state ut (conservative; Sec. 3.4.1):
+// the flux Jacobian A = R Lambda L of that direction, Phi = L (rows: left eigenvectors) and
+// Phi^{-1} = R (columns: right eigenvectors).  Waves u_n - c, entropy, the shear waves of the
+// tangential axes in increasing order, u_n + c; b1 = (gamma-1)/c^2, b2 = b1 |u|^2/2, H = (E+p)/rho.
+template <int D>
+__device__ __forceinline__ void char_matrices(const double* ut, double gamma, int dir, double (&L)[D + 2][D + 2],
+                                              double (&Rm)[D + 2][D + 2]) {
+  constexpr int NV = D + 2;
+  const double rho = ut[0], irho = 1.0 / rho;
+  double u[3] = {0.0, 0.0, 0.0}, q2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    u[k] = ut[1 + k] * irho;
+    q2 = fma(u[k], u[k], q2);
+  }
+  const double p = (gamma - 1.0) * fma(-0.5 * rho, q2, ut[NV - 1]);
+  const double c = sqrt(gamma * p * irho), ic = 1.0 / c, H = (ut[NV - 1] + p) * irho;
+  const double b1 = (gamma - 1.0) * ic * ic, b2 = 0.5 * b1 * q2, un = u[dir];
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) L[i][j] = Rm[i][j] = 0.0;
+  Rm[0][0] = Rm[0][1] = Rm[0][NV - 1] = 1.0;
+  L[0][0] = 0.5 * (b2 + un * ic);
+  L[1][0] = 1.0 - b2;
+  L[NV - 1][0] = 0.5 * (b2 - un * ic);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double nk = (k == dir) ? 1.0 : 0.0;
+    Rm[1 + k][0] = u[k] - c * nk;
+    Rm[1 + k][1] = u[k];
+    Rm[1 + k][NV - 1] = u[k] + c * nk;
+    L[0][1 + k] = 0.5 * (-b1 * u[k] - nk * ic);
+    L[1][1 + k] = b1 * u[k];
+    L[NV - 1][1 + k] = 0.5 * (-b1 * u[k] + nk * ic);
+  }
+  Rm[NV - 1][0] = H - c * un;
+  Rm[NV - 1][1] = 0.5 * q2;
+  Rm[NV - 1][NV - 1] = H + c * un;
+  L[0][NV - 1] = 0.5 * b1;
+  L[1][NV - 1] = -b1;
+  L[NV - 1][NV - 1] = 0.5 * b1;
+  int w = 2;
+#pragma unroll
+  for (int t = 0; t < D; ++t) {
+    if (t == dir) continue;
+    Rm[1 + t][w] = 1.0;
+    Rm[NV - 1][w] = u[t];
+    L[w][0] = -u[t];
+    L[w][1 + t] = 1.0;
+    ++w;
+  }
+}
+
+// WENO-AO Riemann states of one cell in characteristic variables (Sec. 3.4.1): for each direction,
+// the stencil in that direction's characteristic variables, smoothness indicators and nonlinear
+// weights per characteristic component (Eqs. 22, 24, 25), the WENO-AO values (Eq. 19) at the Gauss
+// points of the two faces normal to it only, and the back transform with R.  The weights are
+// computed once per direction: d times the work of the linearized primitive variables.
+template <int D, int R, class WF>
+__device__ __forceinline__ void recon_cell_char(const GridArgs& a, const WF& W, const double* __restrict__ sm, int c,
+                                                double* __restrict__ gs, double* __restrict__ faces, long long cell,
+                                                long long ncell) {
+  using G = Geo<D, R>;
+  using T = Tile<D, R>;
+  constexpr int NV = G::NV, NQ = G::NQ, F = G::F, M = G::M, NT = G::NT, SN = T::SN;
+  constexpr int TS = Cfg64<D, R>::kThreads;
+  const Plan<D, R>& P = c_plan<D, R>;
+  double ut[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ut[v] = sm[v * SN + c];
+#pragma unroll 1
+  for (int dir = 0; dir < D; ++dir) {
+    double L[NV][NV], Rm[NV][NV];
+    char_matrices<D>(ut, a.gamma, dir, L, Rm);
+    double wv[2 * NT][NV];  // characteristic values at this direction's face points
+#pragma unroll 1
+    for (int v = 0; v < NV; ++v) {
+      // ---- g = row v of L applied to every stencil cell ----
+#pragma unroll 4
+      for (int l = 0; l < G::N0; ++l) {
+        const int o = c + P.delta[l];
+        double val = 0.0;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) val = fma(L[v][j], sm[j * SN + o], val);
+        gs[l * TS] = val;
+      }
+      // ---- smoothness indicators and nonlinear weights of this component ----
+      double om[NQ], sum = 0.0;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int nq = P.len[q], base = P.woff[q] + F * nq;
+        const int* idx = P.idx + P.start[q];
+        double b = 0.0;
+#pragma unroll 1
+        for (int m = 0; m < M; ++m) {
+          double d = 0.0;
+#pragma unroll 4
+          for (int j = 0; j < nq; ++j) d = fma(W(base + m * nq + j), gs[idx[j] * TS], d);
+          b = fma(d, d, b);
+        }
+        om[q] = linear_weight<D>(q) / fma(b, b, a.eps);
+        sum += om[q];
+      }
+      double coef[NQ];
+      {
+        const double inv = 1.0 / sum;
+        const double w0 = om[0] * inv;
+        coef[0] = w0 / linear_weight<D>(0);
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) coef[q] = om[q] * inv - w0 * (linear_weight<D>(q) / linear_weight<D>(0));
+      }
+      // ---- WENO-AO values at the Gauss points of the faces normal to dir ----
+#pragma unroll 1
+      for (int k = 0; k < 2 * NT; ++k) {
+        const int sp = 2 * dir * NT + k;
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int nq = P.len[q], base = P.woff[q] + sp * nq;
+          const int* idx = P.idx + P.start[q];
+          double val = 0.0;
+#pragma unroll 4
+          for (int j = 0; j < nq; ++j) val = fma(W(base + j), gs[idx[j] * TS], val);
+          acc = fma(coef[q], val, acc);
+        }
+        wv[k][v] = acc;
+      }
+    }
+    // ---- back to conservative variables, u_s = R w_s ----
+#pragma unroll 1
+    for (int k = 0; k < 2 * NT; ++k) {
+      const int sp = 2 * dir * NT + k;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        double out = 0.0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out = fma(Rm[j][v], wv[k][v], out);
+        faces[((long long)sp * NV + j) * ncell + cell] = out;
+      }
+    }
+  }
+}
+
 // Positivity-preserving limiter of Sec. 4 on the F Riemann states of one cell.
 template <int D, int R>
 __device__ __forceinline__ void limit_cell(const GridArgs& a, const double* __restrict__ sm,
@@ -296,7 +443,9 @@ struct WFun {
   }
 };
 
-template <int D, int R, bool P>
+// CHAR: WENO-AO cells in characteristic variables (a separate instantiation, so that the
+// linearized-primitive kernel keeps its register allocation)
+template <int D, int R, bool P, bool CHAR>
 __global__ void __launch_bounds__(Cfg64<D, R>::kThreads) recon64_kernel(GridArgs a, int mode,
                                                                         const double* __restrict__ U,
                                                                         double* __restrict__ faces,
@@ -353,6 +502,8 @@ __global__ void __launch_bounds__(Cfg64<D, R>::kThreads) recon64_kernel(GridArgs
     const bool linear = (mode == 1) || (mode >= 2 && gate_mask[cell]);
     if (linear)
       recon_cell<D, R, true>(a, W, sm, c, gs + tid, faces, fc, ncell_f);
+    else if constexpr (CHAR)
+      recon_cell_char<D, R>(a, W, sm, c, gs + tid, faces, fc, ncell_f);
     else
       recon_cell<D, R, false>(a, W, sm, c, gs + tid, faces, fc, ncell_f);
     if (a.positivity) limit_cell<D, R>(a, sm, sp, c, faces, fc, ncell_f);
@@ -379,7 +530,7 @@ cudaError_t launch_dr(kfvm_ctx* ctx, const double* U, double* faces, cudaStream_
   const int tiles = ((ctx->n[0] + T::TX - 1) / T::TX) * ((ctx->n[1] + T::TY - 1) / T::TY) *
                     ((D == 3) ? (zf_count + T::TZ - 1) / T::TZ : 1);
   const size_t smem = sizeof(double) * ((Geo<D, R>::NV + 1) * T::SN + Geo<D, R>::N0 * TS);
-  auto kern = recon64_kernel<D, R, P>;
+  auto kern = ctx->vars == 1 ? recon64_kernel<D, R, P, true> : recon64_kernel<D, R, P, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   std::unique_ptr<WParam<D, R, P>> wp(new WParam<D, R, P>);  // host staging of the parameter copy
