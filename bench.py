@@ -222,19 +222,24 @@ def flush_l2(buf):
 
 
 def time_steps(g, U, steps, stream, flush_buf):
-    """Per-step CUDA events on the launching stream; L2 flushed between steps (outside the events)."""
+    """Per-step CUDA events on the launching stream, each step behind an L2 flush that lies outside its
+    events.  The steps are enqueued back to back and the stream is synchronised once at the end, so the
+    device never waits inside a timed step for the host to issue its launches (a per-step wait would
+    put the host's launch latency of every step's first kernel inside the events)."""
     import torch
-    total = 0.0
-    for _ in range(steps):
+    pairs = []
+    for k in range(steps):
         flush_l2(flush_buf)
+        if k == 0:
+            flush_l2(flush_buf)  # a longer lead for the first step, while the host issues its launches
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         g.step(U, CFL, sync=False, stream=stream)
         e1.record(stream)
-        e1.synchronize()
-        total += e0.elapsed_time(e1)
-    return total  # ms
+        pairs.append((e0, e1))
+    stream.synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in pairs)  # ms
 
 
 def make_solver(W, path, n=None):
@@ -334,8 +339,6 @@ def measure_path(W, path, U0, steps, warmup, stream, flush_buf, n=None, min_warm
         U.copy_(U0)
         torch.cuda.synchronize()
         launches0 = g.launches
-        g.set_option("profile", 1)
-        g.profile_reset()
         if barrier is not None:
             barrier()
         torch.cuda.synchronize()
@@ -343,11 +346,20 @@ def measure_path(W, path, U0, steps, warmup, stream, flush_buf, n=None, min_warm
         torch.cuda.synchronize()
         if barrier is not None:
             barrier()
-        prof = g.profile()
-        g.set_option("profile", 0)
         launches = g.launches - launches0
         g.sync_status(stream)
-    return g, ms, prof, launches, U
+        U_final = U.clone()
+        # the same steps again from the same state with the library's per-launch event tracing on
+        # (kernel durations and shares; the tracing events would otherwise sit inside the timed steps)
+        U.copy_(U0)
+        g.set_option("profile", 1)
+        g.profile_reset()
+        time_steps(g, U, steps, stream, flush_buf)
+        torch.cuda.synchronize()
+        prof = g.profile()
+        g.set_option("profile", 0)
+        g.sync_status(stream)
+    return g, ms, prof, launches, U_final
 
 
 def main():

@@ -2,8 +2,8 @@
 
     python -m paper_2401_16543_gb300.kernel_tour
 
-Launches, in order: the FP64 path (build_weights, max_rate, recon64, flux_update) and the flux-only
-entry (face_flux, update) on 2D 256^2; the FP32 path in 3D radius 2 (shadow, recon32<3,2>,
+Launches, in order: the FP64 path (build_weights, max_rate, recon64, flux_update), the flux-only
+entry (face_flux, update) and recon64 in characteristic variables on 2D 256^2; the FP32 path in 3D radius 2 (shadow, recon32<3,2>,
 flux_update) on 48^3; 3D radius 3 on 32^3 (recon33 on the FP32 pipe, recon33_tc on the tensor
 cores, label33); the learned gate (features, label, forward, mask, train, adam) and the KXRCF
 indicator (float64 and float32) on the 2D grid.
@@ -33,6 +33,10 @@ def main() -> None:
     g.step(U2.clone(), 0.4)
     faces = g.reconstruct(U2)
     g.flux(faces)
+    # WENO-AO in characteristic variables (Sec. 3.4.1), FP64
+    g.set_option("variables", 1)
+    g.reconstruct(U2)
+    g.set_option("variables", 0)
     # the gate on the 2D grid (features + labels, forward, training step, the mask of the gated step)
     g.set_option("precision", 32)
     g.gate_set_params(np.load(os.path.join(HERE, "gate_params_2d.npy")))
