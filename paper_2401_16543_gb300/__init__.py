@@ -21,7 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "_build", "libkfvm.so")
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "singular weight system",
-          4: "non-admissible state", 5: "call out of order", 6: "device wait timed out", 7: "out of memory"}
+          4: "non-admissible state", 5: "call out of order", 6: "device wait timed out", 7: "out of memory",
+          8: "problem exceeds a fixed-size buffer"}
 BC = {"periodic": 0, "outflow": 1}
 
 
