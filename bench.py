@@ -476,7 +476,7 @@ def main():
     traffic = None
     launches_per_stage = n_launch / (3 * args.steps) if n_launch else 1
     tfile = os.path.join(ROOT, "profiles", f"{kern}_{W.name}_traffic.txt")
-    if os.path.exists(tfile):
+    if os.path.exists(tfile) and path != "fp64char":  # the capture is of the linearized-primitive kernel
         for line in open(tfile):
             if line.startswith("traffic_bytes_per_launch"):
                 traffic = float(line.split("=")[1])
