@@ -17,11 +17,12 @@
 // ghost-cell map) sit in shared memory.  The directions are taken one at a
 // time: the tile's cells and the ring of cells just outside it along that
 // direction (one thread each: the block has as many threads as the largest such
-// set, so the ring is no second wave) reconstruct their faces normal to it (the
-// ring only the face it shares with the tile) and park q at those points in
-// shared memory, numbered with x fastest so that a warp reads consecutive
-// cells; then every tile cell compares its two faces with its neighbours'.  Each face
-// state is computed once per direction instead of once per side.  T = double
+// set, so the ring is no second wave) reconstruct their two faces normal to it
+// in one pass over the stencil (a ring cell keeps only the face it shares with
+// the tile) and park q at those points in shared memory, numbered with x
+// fastest so that a warp reads consecutive cells; then every tile cell compares
+// its two faces with its neighbours'.  Each face state is computed once per
+// direction instead of once per side.  T = double
 // reads the float64 state (FP64 mode); T = float reads its float32 shadow (FP32
 // mode), so the decision is taken in the precision of the path it serves.
 #include <cuda_runtime.h>
