@@ -70,3 +70,11 @@ def test_fp32_refuses_characteristic_variables(kfvm):
     with pytest.raises(kfvm.KfvmError) as e:
         g.reconstruct(U)
     assert e.value.code == 5  # KFVM_ERR_STATE
+
+
+def test_variables_option_is_checked(kfvm):
+    g = kfvm.KFVM([16, 16], dims=2, radius=2, bc="outflow")
+    for bad in (2.0, -1.0, 0.5):
+        with pytest.raises(kfvm.KfvmError) as e:
+            g.set_option("variables", bad)
+        assert e.value.code == 1  # KFVM_ERR_ARG

@@ -153,3 +153,20 @@ def test_kxrcf_path_on_smooth_translation(kfvm):
     assert e["kx64"] < e["weno64"], e
     rel = np.abs(res["kx32"] - res["kx64"]).sum() / np.abs(res["kx64"]).sum()
     assert rel <= 1e-6, rel
+
+
+def test_kxrcf_options_are_checked(kfvm):
+    """"recon" 4 selects the KXRCF mode; "kxrcf_m" accepts 0 < m <= 16 and changes the decisions."""
+    g = kfvm.KFVM([40, 24], dims=2, radius=2, bc="outflow")
+    for bad in (0.0, -1.0, 17.0):
+        with pytest.raises(kfvm.KfvmError) as e:
+            g.set_option("kxrcf_m", bad)
+        assert e.value.code == 1  # KFVM_ERR_ARG
+    with pytest.raises(kfvm.KfvmError):
+        g.set_option("recon", 3)  # the caller-mask mode is set by kfvm_set_smooth_mask only
+    U = workloads.mixed_voronoi(2, 40, 6, seed=3)[:, :24, :40].contiguous().cuda()  # smooth and constant regions
+    g.set_option("kxrcf_m", 1.5)
+    m15 = g.kxrcf_mask(U).cpu().numpy()
+    g.set_option("kxrcf_m", 4.0)  # a smaller threshold Delta^m flags more cells
+    m40 = g.kxrcf_mask(U).cpu().numpy()
+    assert (m40 <= m15).all() and m40.sum() < m15.sum()
