@@ -218,13 +218,13 @@ def _brute_force_ratio(U, bc, R, m_pow=1.5, hi=(1.0, 1.0)):
     return ratio, ratio < max(dx, dy) ** m_pow
 
 
-@pytest.mark.parametrize("bc", ["outflow", "periodic"])
-def test_ratio_matches_brute_force_by_position(bc):
+@pytest.mark.parametrize("bc,R", [("outflow", 2), ("periodic", 2), ("outflow", 3)])
+def test_ratio_matches_brute_force_by_position(bc, R):
     nx, ny = 7, 6
     U = np.ascontiguousarray(workloads.mixed_voronoi(2, 8, 4, seed=21).numpy()[:, :ny, :nx])
-    o = oracle.Oracle([nx, ny], dim=2, R=2, bc=bc)
+    o = oracle.Oracle([nx, ny], dim=2, R=R, bc=bc)
     r, m = o.kxrcf(U)
-    rb, mb = _brute_force_ratio(U, bc, 2)
+    rb, mb = _brute_force_ratio(U, bc, R)
     fin = np.isfinite(rb)
     assert (np.isfinite(r) == fin).all()
     scale = np.maximum(rb[fin], 1e-9)
