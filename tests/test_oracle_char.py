@@ -153,3 +153,33 @@ def test_y_aligned_problem_is_the_transposed_x_problem():
     Vy, _, _ = oy.run(V, 0.4, 0.05)
     back = np.stack([Vy[0].T, Vy[2].T, Vy[1].T, Vy[3].T])
     assert np.abs(Ux - back).max() < 1e-13
+
+
+def test_z_aligned_problem_is_the_permuted_x_problem():
+    """3D: the Sod-like problem along z, with x and z (and their momenta) exchanged, gives the
+    permuted solution of the problem along x: the z faces take the z direction's eigenvectors."""
+    n, m = 16, 3
+    x = (np.arange(n) + 0.5) / n
+    rho = np.where(x < 0.5, 1.0, 0.125)
+    p = np.where(x < 0.5, 1.0, 0.1)
+    u, v, w = 0.3, 0.2, -0.1
+    U = np.zeros((5, m, m, n))  # [var][z][y][x], varying along x
+    U[0] = rho
+    U[1] = rho * u
+    U[2] = rho * v
+    U[3] = rho * w
+    U[4] = p / (G - 1) + 0.5 * rho * (u * u + v * v + w * w)
+    ox = oracle.Oracle([n, m, m], dim=3, R=2, hi=[1.0, m / n, m / n],
+                       bc=[("outflow", "outflow"), ("periodic", "periodic"), ("periodic", "periodic")],
+                       variables="characteristic")
+    oz = oracle.Oracle([m, m, n], dim=3, R=2, hi=[m / n, m / n, 1.0],
+                       bc=[("periodic", "periodic"), ("periodic", "periodic"), ("outflow", "outflow")],
+                       variables="characteristic")
+    # exchange x and z: array axes (z, y, x) -> (x, y, z), momenta m_x <-> m_z
+    V = np.ascontiguousarray(np.stack([U[0].transpose(2, 1, 0), U[3].transpose(2, 1, 0), U[2].transpose(2, 1, 0),
+                                       U[1].transpose(2, 1, 0), U[4].transpose(2, 1, 0)]))
+    Ux, _, _ = ox.run(np.ascontiguousarray(U), 0.4, 0.05)
+    Vz, _, _ = oz.run(V, 0.4, 0.05)
+    back = np.stack([Vz[0].transpose(2, 1, 0), Vz[3].transpose(2, 1, 0), Vz[2].transpose(2, 1, 0),
+                     Vz[1].transpose(2, 1, 0), Vz[4].transpose(2, 1, 0)])
+    assert np.abs(Ux - back).max() < 1e-13
