@@ -48,7 +48,10 @@ def test_smooth_translation_3d_error_not_worse_than_fp64_weno(kfvm, tc, bound):
     mixes linear and WENO-AO cells measures 8% (FP32-pipe contraction) / 11% (tensor-core
     contraction, Riemann states within 1.4x the FP32 pipe's rounding on this data) above the
     all-WENO error.  Neither the 2D gate's gain (a ~10x smaller error) nor the 1e-6 bar holds in this case;
-    the bound records that."""
+    the bound records that.  The cause is the linear operator: at radius 3 in 3D the linear S0
+    reconstruction with SSP-RK3 is not stable at CFL 0.4 (all cells linear: L1 7-10x the WENO-AO
+    error here, test_gpu_kxrcf.py), so linear cells in smooth regions lean on the WENO-AO cells
+    around them."""
     n, t_end = 32, 0.05
     U0 = workloads.sine_3d(n)
     ex = workloads.sine_3d_exact_density(n, t_end)
