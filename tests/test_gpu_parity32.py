@@ -3,8 +3,9 @@
 Tolerances follow from the arithmetic (the CFL rate is formed in float32, so dt
 agrees to 1e-6): the float32 shadow of the state carries a
 relative rounding of 2^-24 ~ 6e-8; each Riemann-state value is a contraction
-whose weights sum in absolute value to at most ~3 (2D) / ~6 (3D), so its error
-is a few 1e-7 of the state's magnitude; the nonlinear weights and the limiter's
+whose weights sum in absolute value to ~2-3.3 (2D, 3D radius 2), so its error
+is a few 1e-7 of the state's magnitude (the S0 face rows of 3D radius 3 sum to
+~70: a few 1e-6 there); the nonlinear weights and the limiter's
 theta factors move by O(1e-6) relative.  Face states are checked at 2e-5 of the
 state's magnitude, one SSP-RK3 step at 2e-6 (the update is dt*L with
 dt*|L| ~ CFL * |U|, accumulated in float64).  The accuracy target of the
