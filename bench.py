@@ -2,13 +2,18 @@
 """Throughput of the KFVM-WENO hot path on one GB300 (or N replicas under torchrun).
 
 Metric: cell-updates/s per RK stage (cells x RK stages / time) of SSP-RK3 steps.
-The default workload is the 2D Euler problem on 1024 x 1024 cells: radius-2
-KFVM-WENO-AO, HLLC, the positivity limiter, outflow boundaries, 64 seeded
-Voronoi regions with rho, p ~ U[0.1, 1] and u, v ~ U[-1, 1] (seed 2), CFL 0.4.
-``--workload`` selects the other synthetic workloads (3D 256^3 half smooth /
-half Voronoi at radius 2; 2D 2048^2 mixed smooth/constant regions; 3D 512^3
-mixed regions at radius 3, whose plain FP64 comparison runs on a slab of
-z-planes because that path takes seconds per stage).
+The default workload is the 3D Euler problem on 512^3 cells at radius 3: the
+learned gate + mixed-precision path (FP32 Riemann states, the contraction on
+the tcgen05 tensor cores, float64 accumulation) against the plain FP64 GPU
+path, 512 seeded Voronoi regions each carrying the smooth sine-advection state
+or a random constant (seed 5), outflow boundaries, CFL 0.4.  The plain FP64
+comparison runs on the first 16 z-planes of the same state (that path takes
+seconds per stage at full size).  ``matched_l1`` reports the accuracy side of
+the metric on the smooth-translation check of the same dimension and radius:
+the gated path's L1 density error against the exact solution over the plain
+FP64 WENO-AO path's.  ``--workload`` selects the other synthetic workloads
+(2D 1024^2 Voronoi; 3D 256^3 half smooth / half Voronoi at radius 2; 2D
+2048^2 mixed smooth/constant regions; 3D 64^3 radius 3).
 
 One printed JSON line (rank 0).  A "step" is one SSP-RK3 step: the CFL
 reduction and three RK stages (Riemann states, face fluxes, update), all in the
@@ -16,8 +21,8 @@ library's kernels.  ``value`` is the headline path with inputs resident in
 HBM; ``fp64_plain`` is the plain FP64 GPU path on the same workload; ``e2e``
 is the headline path through the C ABI with the state copied host->device
 before and device->host after every step; ``cpu_baseline`` is the oracle on
-the host cores.  ``--impl reference`` times the oracle instead (the reference
-arm of this repository).
+the host cores (all of them, OpenMP build, and one thread).  ``--impl reference``
+times the oracle instead (the reference arm of this repository).
 """
 from __future__ import annotations
 
@@ -35,6 +40,7 @@ sys.path.insert(0, ROOT)
 CFL = 0.4
 METRIC = "cell-updates/s per RK stage"
 GATE_THRESHOLD = 0.8
+TRACED_STEPS = 5  # steps of the second, traced pass that gives each kernel's device time
 
 
 class Workload:
@@ -66,33 +72,37 @@ def _workloads():
             "voronoi2d-1024", 2, 2, [1024, 1024], "outflow",
             "2D Euler 1024x1024, radius-2 KFVM-WENO-AO (linearized primitive variables), HLLC + Batten, positivity "
             "limiter, outflow, 64 seeded Voronoi regions (rho,p~U[0.1,1], u,v~U[-1,1], seed 2), SSP-RK3 at CFL 0.4",
-            lambda dev: wl.voronoi_2d(1024, k=64, seed=2, device=dev), gate="gate_params_2d.npy", cpu_crop=128),
+            lambda dev, crop=None: wl.voronoi_2d(1024, k=64, seed=2, device=dev, crop=crop), gate="gate_params_2d.npy",
+            cpu_crop=128),
         "halfsine3d-256": Workload(
             "halfsine3d-256", 3, 2, [256, 256, 256], "periodic",
             "3D Euler 256^3 periodic, radius 2: x<1/2 smooth sine advection, x>=1/2 128 seeded Voronoi regions "
             "(seed 3), FP32 mixed path vs plain FP64, SSP-RK3 at CFL 0.4",
-            lambda dev: wl.half_sine_voronoi_3d(256, k=128, seed=3, device=dev), gate=None, cpu_crop=24),
+            lambda dev, crop=None: wl.half_sine_voronoi_3d(256, k=128, seed=3, device=dev, crop=crop), gate=None,
+            cpu_crop=24),
         "mixed2d-2048": Workload(
             "mixed2d-2048", 2, 2, [2048, 2048], "outflow",
             "2D Euler 2048x2048, radius 2, learned gate: 256 seeded Voronoi regions (seed 4), each smooth sine or a "
             "constant (coin 1/2), outflow, SSP-RK3 at CFL 0.4",
-            lambda dev: wl.mixed_voronoi(2, 2048, 256, seed=4, device=dev), gate="gate_params_2d.npy", cpu_crop=128),
+            lambda dev, crop=None: wl.mixed_voronoi(2, 2048, 256, seed=4, device=dev, crop=crop),
+            gate="gate_params_2d.npy", cpu_crop=128),
         "mixed3d-64-r3": Workload(
             "mixed3d-64-r3", 3, 3, [64, 64, 64], "outflow",
             "3D Euler 64^3, radius 3, learned gate + mixed precision: 8 seeded Voronoi regions (seed 5), each "
             "smooth sine or a constant, outflow, SSP-RK3 at CFL 0.4 (the 512^3 workload's scheme on a grid that "
             "profilers can capture)",
-            lambda dev: wl.mixed_voronoi(3, 64, 8, seed=5, R=3, device=dev), gate="gate_params_3d.npy", cpu_crop=16),
+            lambda dev, crop=None: wl.mixed_voronoi(3, 64, 8, seed=5, R=3, device=dev, crop=crop),
+            gate="gate_params_3d.npy", cpu_crop=16),
         "mixed3d-512-r3": Workload(
             "mixed3d-512-r3", 3, 3, [512, 512, 512], "outflow",
             "3D Euler 512^3, radius 3, learned gate + mixed precision: 512 seeded Voronoi regions (seed 5), each smooth "
             "sine or a constant, outflow, SSP-RK3 at CFL 0.4; plain FP64 timed on 16 z-planes of the same state",
-            lambda dev: wl.mixed_voronoi(3, 512, 512, seed=5, R=3, device=dev), gate="gate_params_3d.npy",
-            fp64_planes=16, cpu_crop=16),
+            lambda dev, crop=None: wl.mixed_voronoi(3, 512, 512, seed=5, R=3, device=dev, crop=crop),
+            gate="gate_params_3d.npy", fp64_planes=16, cpu_crop=24),
     }
 
 
-DEFAULT_WORKLOAD = "voronoi2d-1024"
+DEFAULT_WORKLOAD = "mixed3d-512-r3"
 
 
 def parse():
@@ -128,9 +138,9 @@ def run_reference(args, world, rank):
     import oracle
     W = _workloads()[args.workload]
     crop = W.cpu_crop
-    U = W.make("cpu").numpy()
-    U = np.ascontiguousarray(U[:, :crop, :crop] if W.dims == 2 else U[:, :crop, :crop, :crop])
-    o = oracle.Oracle([crop] * W.dims, dim=W.dims, R=W.R, bc=W.bc)
+    U = np.ascontiguousarray(W.make("cpu", crop=crop).numpy())
+    cores = host_cores()
+    o = oracle.Oracle([crop] * W.dims, dim=W.dims, R=W.R, bc=W.bc, threaded=True)
     for _ in range(args.warmup):
         o.step(U, CFL)
     t0 = time.perf_counter()
@@ -146,8 +156,9 @@ def run_reference(args, world, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": W.desc, "grid": W.n, "radius": W.R,
                    "sample": f"{shape} corner crop of the workload per step"},
-        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"SSP-RK3 steps of a {shape} crop, single-threaded C oracle"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"SSP-RK3 steps of a {shape} corner crop, C oracle (OpenMP build) on {cores} "
+                                   "host cores"},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -156,6 +167,72 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(W, t_budget=10.0):
+    """The oracle on the host cores: one SSP-RK3 step of a corner crop of the workload, on every core
+    (OpenMP build, the value) and on one thread; each repeated until about t_budget seconds."""
+    import numpy as np
+
+    import oracle
+    c = W.cpu_crop
+    U = np.ascontiguousarray(W.make("cpu", crop=c).numpy())
+    shape = [c] * W.dims
+    cells = c ** W.dims
+    out = {}
+    for threaded in (True, False):
+        o = oracle.Oracle(list(shape), dim=W.dims, R=W.R, bc=W.bc, threaded=threaded)
+        k, t0 = 0, time.perf_counter()
+        while True:
+            o.step(U, CFL)
+            k += 1
+            el = time.perf_counter() - t0
+            if el >= t_budget or k >= 50:
+                break
+        out[threaded] = (cells * 3 * k / el, k)
+    cores = host_cores()
+    return {"value": out[True][0], "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "single_thread_value": out[False][0],
+            "sample": f"{out[True][1]} (all cores) / {out[False][1]} (one thread) SSP-RK3 steps of a "
+                      f"{'x'.join(map(str, shape))} corner crop of the workload; C oracle, OpenMP build over "
+                      f"{cores} host cores (value) and the single-threaded build (single_thread_value)"}
+
+
+def matched_l1(pkg, W):
+    """The accuracy side of the metric: L1 density error against the exact solution of the smooth
+    translation (sine advection, periodic) of the workload's dimension and radius, for the headline
+    gated mixed-precision path and the plain FP64 WENO-AO path; ratio = E_gated / E_fp64."""
+    import numpy as np
+
+    import workloads as wl
+    if W.dims == 2:
+        n, t_end = 64, 0.1
+        U0 = wl.sine_2d(n, R=W.R)
+        ex = wl.sine_2d_exact_density(n, t_end)
+    else:
+        n, t_end = 32, 0.05
+        U0 = wl.sine_3d(n, R=W.R)
+        ex = wl.sine_3d_exact_density(n, t_end)
+    errs = {}
+    for path in ("fp64", "gated"):
+        g = make_solver(W, path, [n] * W.dims)
+        if path == "gated":
+            frac = float(g.gate_mask(U0.cuda()).float().mean().item())
+        U = U0.cuda()
+        g.run(U, CFL, t_end)
+        errs[path] = float(np.abs(U[0].cpu().numpy() - ex).mean())
+        del g
+    ratio = errs["gated"] / errs["fp64"]
+    return {"ratio": ratio, "E_gated": errs["gated"], "E_fp64_weno": errs["fp64"], "bar": 1 + 1e-6,
+            "met": bool(ratio <= 1 + 1e-6), "gate_linear_fraction_t0": round(frac, 4),
+            "case": f"{W.dims}D sine translation {n}^{W.dims}, periodic, radius {W.R}, to t = {t_end}, CFL {CFL}"}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled while the GPU is loaded."""
 
@@ -349,12 +426,13 @@ def measure_path(W, path, U0, steps, warmup, stream, flush_buf, n=None, min_warm
         launches = g.launches - launches0
         g.sync_status(stream)
         U_final = U.clone()
-        # the same steps again from the same state with the library's per-launch event tracing on
-        # (kernel durations and shares; the tracing events would otherwise sit inside the timed steps)
+        # the first (at most TRACED_STEPS) of the same steps again from the same state with the library's
+        # per-launch event tracing on (kernel durations and shares; the tracing events would otherwise sit
+        # inside the timed steps)
         U.copy_(U0)
         g.set_option("profile", 1)
         g.profile_reset()
-        time_steps(g, U, steps, stream, flush_buf)
+        time_steps(g, U, min(steps, TRACED_STEPS), stream, flush_buf)
         torch.cuda.synchronize()
         prof = g.profile()
         g.set_option("profile", 0)
@@ -470,50 +548,40 @@ def main():
         flops = ncell * (smooth_frac * algo_flops_per_cell(W.dims, W.R, "linear")
                          + (1 - smooth_frac) * algo_flops_per_cell(W.dims, W.R, "weno"))
     peak_flops = pkg.measure_fma_peak(64 if path.startswith("fp64") else 32)
-    # algorithmic flops of every timed stage over the kernel's summed device time (3D grids above the
+    # algorithmic flops of every traced stage over the kernel's summed device time (3D grids above the
     # Riemann-state buffer run as several launches per stage, one per z-slab)
-    achieved = flops * 3 * args.steps / (kms * 1e-3) if kms > 0 else 0.0
+    traced = min(args.steps, TRACED_STEPS)
+    achieved = flops * 3 * traced / (kms * 1e-3) if kms > 0 else 0.0
     traffic = None
-    launches_per_stage = n_launch / (3 * args.steps) if n_launch else 1
+    launches_per_stage = n_launch / (3 * traced) if n_launch else 1
     tfile = os.path.join(ROOT, "profiles", f"{kern}_{W.name}_traffic.txt")
     if os.path.exists(tfile) and path != "fp64char":  # the capture is of the linearized-primitive kernel
         for line in open(tfile):
             if line.startswith("traffic_bytes_per_launch"):
                 traffic = float(line.split("=")[1])
     total_prof = sum(v[1] for v in prof.values())
-    roofline = {"bound": "alu", "kernel": kern, "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
+    kname = {"recon64": "recon64_kernel", "recon32": "recon32_kernel"}[kern]
+    if kern == "recon32" and W.dims == 3 and W.R == 3:
+        kname = "recon33_tc_kernel (tcgen05)"
+    roofline = {"bound": "alu", "kernel": kern, "kernel_name": kname, "achieved": achieved / 1e12,
+                "peak": peak_flops / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak_flops if peak_flops else None, "traffic": traffic,
                 "peak_source": f"measured live: FP{64 if path.startswith('fp64') else 32} FMA loop on every SM",
                 "algo_flops_per_cell": flops / ncell, "mode": mode, "gated_smooth_fraction": smooth_frac,
                 # the learned gate's own work, on the tensor pipe (not in "achieved", which is FP32-pipe work)
                 "gate_tensor_flops_per_cell": gate_flops_per_cell(W.dims) if path == "gated" else None,
-                "achieved_incl_gate_tflops": ((flops + gate_flops_per_cell(W.dims) * ncell) * 3 * args.steps
+                "achieved_incl_gate_tflops": ((flops + gate_flops_per_cell(W.dims) * ncell) * 3 * traced
                                               / (kms * 1e-3) / 1e12) if (path == "gated" and kms > 0) else None,
                 "launches_per_stage": launches_per_stage,
                 "kernel_share": {k: round(v[1] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
 
+    # ---- the accuracy side of the metric ----
+    l1 = matched_l1(pkg, W) if (rank == 0 and path == "gated") else None
+
     # ---- the oracle on the host cores ----
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        import numpy as np
-
-        import oracle
-        if W.name == DEFAULT_WORKLOAD:
-            Un, shape = U0.cpu().numpy(), W.n
-        else:
-            c = W.cpu_crop
-            Un = U0[:, :c, :c].cpu().numpy() if W.dims == 2 else U0[:, :c, :c, :c].cpu().numpy()
-            shape = [c] * W.dims
-        o = oracle.Oracle(list(shape), dim=W.dims, R=W.R, bc=W.bc)
-        t0 = time.perf_counter()
-        o.step(np.ascontiguousarray(Un), CFL)
-        el = time.perf_counter() - t0
-        cells = 1
-        for v in shape:
-            cells *= v
-        cpu = {"value": cells * 3 / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"one SSP-RK3 step (3 RK stages) of {'x'.join(map(str, shape))} cells of the workload, "
-                         "single-threaded C oracle"}
+        cpu = cpu_baseline(W)
 
     if rank == 0:
         line = {
@@ -530,6 +598,7 @@ def main():
             "fp64_plain": fp64,
             "other_paths": others,
             "speedup_vs_fp64": value / fp64["value"],
+            "matched_l1": l1,
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
             "kernel_ms": {k: round(v[1], 4) for k, v in prof.items()}, "clocks": clocks,
         }

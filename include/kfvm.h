@@ -192,7 +192,7 @@ kfvm_status kfvm_flux(kfvm_ctx* ctx, const void* faces, double* dUdt, void* stre
  * 16 MiB (plus a 256-byte status word) that every GPU loading the library
  * holds until the process exits.  Problems whose fluxes need more,
  * (dims+2) * sum_d (n_d+1) * prod_{e != d} n_e * 8 bytes > 16 MiB
- * (in 2D about 510 x 510 cells, in 3D about 96^3), are rejected with
+ * (in 2D up to 511 x 511 cells, in 3D up to 51^3), are rejected with
  * KFVM_ERR_TOO_LARGE before any device work.  Nothing is allocated: no
  * cudaMalloc, no cudaFree, no allocating library routine.  The first call
  * made with a given device current looks up the array's device address

@@ -59,13 +59,14 @@ class _Problem(ctypes.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = ctypes.CDLL(_build())
+def lib(threaded: bool = False):
+    """The oracle's C library; ``threaded`` loads the OpenMP timing build of the same source (equal
+    results, cell loops over all host cores), used only to time the oracle on every core."""
+    if threaded not in _libs:
+        L = ctypes.CDLL(_build(threaded=threaded))
         L.kfo_weights.argtypes = [_I, _I, _D, _I, _PI, _I, _PI, _I, _PI, _PD, _PD]
         L.kfo_weights.restype = _I
         L.kfo_face_points.argtypes = [_I, _I, _PD]
@@ -93,8 +94,8 @@ def lib():
         L.kfo_char.restype = None
         L.kfo_riemann.argtypes = [_I, _D, _I, _I, _PD, _PD, _PD]
         L.kfo_riemann.restype = _I
-        _lib = L
-    return _lib
+        _libs[threaded] = L
+    return _libs[threaded]
 
 
 def _pd(a):
@@ -186,14 +187,16 @@ class Oracle:
     """One grid + scheme configuration.
 
     State arrays are float64 with shape (nv, ny, nx) in 2D and (nv, nz, ny, nx)
-    in 3D, variables (rho, rho u, rho v[, rho w], E), x fastest.
+    in 3D, variables (rho, rho u, rho v[, rho w], E), x fastest.  ``threaded``
+    makes ``step`` use the OpenMP timing build (same results on every core).
     """
 
     def __init__(self, n, dim: int = 2, R: int = 2, lo=None, hi=None, bc="periodic", gamma: float = 1.4,
                  ell: float = 5.0, eps: float = 1e-40, recon: str = "weno", riemann: str = "hllc",
                  positivity: bool = True, kappa: float = 0.1, eta: float = 0.0, mask=None,
-                 kxrcf_m: float = 1.5, variables: str = "linprim"):
+                 kxrcf_m: float = 1.5, variables: str = "linprim", threaded: bool = False):
         self.dim, self.R, self.nv = dim, R, dim + 2
+        self._threaded = bool(threaded)
         n = list(n) + [1] * (3 - len(n))
         lo = list(lo) if lo is not None else [0.0] * dim
         hi = list(hi) if hi is not None else [1.0] * dim
@@ -294,7 +297,8 @@ class Oracle:
         """One SSP-RK3 step; returns (U_new, dt)."""
         U = self._state(U).copy()
         dt = _D(0.0)
-        self.status = lib().kfo_step(ctypes.byref(self._pb), _pd(U), float(cfl), float(t_rem), ctypes.byref(dt))
+        self.status = lib(self._threaded).kfo_step(ctypes.byref(self._pb), _pd(U), float(cfl), float(t_rem),
+                                                   ctypes.byref(dt))
         return U, dt.value
 
     def run(self, U, cfl: float, t_end: float, max_steps: int = 10 ** 9):

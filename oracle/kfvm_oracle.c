@@ -48,6 +48,12 @@
  *   kfo_step         SSP-RK3 (Shu-Osher) with dt = CFL / max_cells
  *                    sum_d (|u_d| + c)/Delta_d, clipped to the time left.
  *
+ * Threads: compiled as it is (the checker library) everything runs on one
+ * thread.  The cell loops carry OpenMP work-sharing pragmas that only the
+ * separate timing build (-fopenmp, used for the all-core CPU baseline) turns
+ * on; every cell is still computed by the same statements in the same order,
+ * so both builds give the same bits.
+ *
  * Layouts: the state is SoA [var][z][y][x] (x fastest).  Face states are
  * [point][var][cell] with point = (dir*2 + side)*R^(dim-1) + t, side 0 the
  * low face (x_dir = -1/2), t = t0 + R*t1 over the transverse axes in
@@ -57,6 +63,14 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#define KFO_MAX_THREADS() omp_get_max_threads()
+#define KFO_THREAD() omp_get_thread_num()
+#else
+#define KFO_MAX_THREADS() 1
+#define KFO_THREAD() 0
+#endif
 
 #if defined(__aarch64__) && (LDBL_MANT_DIG == 113)
 typedef long double qreal;
@@ -456,16 +470,27 @@ int kfo_reconstruct(const kfo_problem* pb, const double* U, double* faces, doubl
     free(kmask);
     return sk;
   }
-  double* sten = (double*)malloc(sizeof(double) * n0 * nv); /* [l][var] conservative */
-  double* W = (double*)malloc(sizeof(double) * n0 * nv);    /* [var][l] reconstruction variables */
-  double* vals = (double*)malloc(sizeof(double) * nq * F);  /* v_q(s) for one variable */
-  double* ws = (double*)malloc(sizeof(double) * F * nv);    /* w_s [s][var] */
-  if (!sten || !W || !vals || !ws) { free(sten); free(W); free(vals); free(ws); return KFO_ERR_NOMEM; }
+  /* per-thread scratch (one thread in the checker build) */
+  const int nth = KFO_MAX_THREADS();
+  double* sten_all = (double*)malloc(sizeof(double) * n0 * nv * nth); /* [l][var] conservative */
+  double* W_all = (double*)malloc(sizeof(double) * n0 * nv * nth);    /* [var][l] reconstruction variables */
+  double* vals_all = (double*)malloc(sizeof(double) * nq * F * nth);  /* v_q(s) for one variable */
+  double* ws_all = (double*)malloc(sizeof(double) * F * nv * nth);    /* w_s [s][var] */
+  if (!sten_all || !W_all || !vals_all || !ws_all) {
+    free(sten_all); free(W_all); free(vals_all); free(ws_all);
+    return KFO_ERR_NOMEM;
+  }
 
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) reduction(max : status)
   for (int z = 0; z < pb->n[2]; ++z)
     for (int y = 0; y < pb->n[1]; ++y)
       for (int x = 0; x < pb->n[0]; ++x) {
         const long c = ((long)z * pb->n[1] + y) * pb->n[0] + x;
+        const int th = KFO_THREAD();
+        double* sten = sten_all + (long)th * n0 * nv;
+        double* W = W_all + (long)th * n0 * nv;
+        double* vals = vals_all + (long)th * nq * F;
+        double* ws = ws_all + (long)th * F * nv;
         /* gather S0 through the ghost-cell map */
         for (int l = 0; l < n0; ++l) {
           int ix = map_index(x + pb->offs[3 * l + 0], pb->n[0], pb->bc[0][0], pb->bc[0][1]);
@@ -555,10 +580,10 @@ int kfo_reconstruct(const kfo_problem* pb, const double* U, double* faces, doubl
           for (int v = 0; v < nv; ++v) faces[((long)s * nv + v) * nc + c] = ws[s * nv + v];
         }
       }
-  free(sten);
-  free(W);
-  free(vals);
-  free(ws);
+  free(sten_all);
+  free(W_all);
+  free(vals_all);
+  free(ws_all);
   return status;
 }
 
@@ -582,6 +607,7 @@ int kfo_limit(const kfo_problem* pb, const double* U, double* faces) {
   const int dim = pb->dim, nv = pb->nv, F = pb->nface;
   const long nc = ncell_of(pb);
   int status = KFO_OK;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) reduction(max : status)
   for (int z = 0; z < pb->n[2]; ++z)
     for (int y = 0; y < pb->n[1]; ++y)
       for (int x = 0; x < pb->n[0]; ++x) {
@@ -716,6 +742,7 @@ int kfo_flux(const kfo_problem* pb, const double* faces, double* dUdt) {
   const int nt = (dim == 2) ? R : R * R;
   int status = KFO_OK;
   for (long i = 0; i < (long)nv * nc; ++i) dUdt[i] = 0;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) reduction(max : status)
   for (int z = 0; z < pb->n[2]; ++z)
     for (int y = 0; y < pb->n[1]; ++y)
       for (int x = 0; x < pb->n[0]; ++x) {
@@ -873,10 +900,13 @@ int kfo_step(const kfo_problem* pb, double* U, double cfl, double t_rem, double*
   if (!Un || !L || !Us) { free(Un); free(L); free(Us); return KFO_ERR_NOMEM; }
   memcpy(Un, U, sizeof(double) * nn);
   int st = kfo_rhs(pb, Un, L);
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < nn; ++i) Us[i] = Un[i] + dt * L[i];
   st |= kfo_rhs(pb, Us, L);
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < nn; ++i) Us[i] = 0.75 * Un[i] + 0.25 * (Us[i] + dt * L[i]);
   st |= kfo_rhs(pb, Us, L);
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < nn; ++i) U[i] = (1.0 / 3.0) * Un[i] + (2.0 / 3.0) * (Us[i] + dt * L[i]);
   free(Un);
   free(L);

@@ -204,16 +204,20 @@ def _nearest_site(coords, sites_t):
     return out.reshape(coords[0].shape)
 
 
-def _voronoi_state(dim, n, lo, hi, sites, states, R, device, smooth_mask_fn=None):
+def _voronoi_state(dim, n, lo, hi, sites, states, R, device, smooth_mask_fn=None, crop=None):
     """Cell averages of the piecewise state.
 
     A cell whose 3^d neighbouring centres share one region (and one side of the
     x = 1/2 plane, when a mask is given) lies wholly in that region, so it takes
     the region's constant, or the Gauss-Legendre average of the sine state.
     Only the remaining cells are averaged point by point with a region lookup.
+    ``crop`` (cells per axis) generates only the corner block [0, crop)^d of the
+    n^d grid: the same values as the corner of the full state.
     """
     nv = dim + 2
     dx = [(hi[a] - lo[a]) / n[a] for a in range(dim)]
+    if crop is not None:
+        n = [min(int(crop), n[a]) for a in range(dim)]
     sites_t = torch.tensor(sites, dtype=torch.float64, device=device)
     table = torch.zeros((len(states), nv), dtype=torch.float64, device=device)
     smooth = torch.zeros(len(states), dtype=torch.bool, device=device)
@@ -271,26 +275,26 @@ def _voronoi_state(dim, n, lo, hi, sites, states, R, device, smooth_mask_fn=None
     return out
 
 
-def voronoi_2d(n: int, k: int = 64, seed: int = 2, R: int = 2, device="cpu") -> torch.Tensor:
+def voronoi_2d(n: int, k: int = 64, seed: int = 2, R: int = 2, device="cpu", crop=None) -> torch.Tensor:
     """C2 family: k constant Voronoi regions on [0,1]^2 (outflow boundaries)."""
     rng = SplitMix64(seed)
     sites, states = _draw_regions(rng, k, 2, [0.0, 0.0], [1.0, 1.0], with_coin=False)
-    return _voronoi_state(2, [n, n], [0.0, 0.0], [1.0, 1.0], sites, states, R, device)
+    return _voronoi_state(2, [n, n], [0.0, 0.0], [1.0, 1.0], sites, states, R, device, crop=crop)
 
 
-def half_sine_voronoi_3d(n: int, k: int = 128, seed: int = 3, R: int = 2, device="cpu") -> torch.Tensor:
+def half_sine_voronoi_3d(n: int, k: int = 128, seed: int = 3, R: int = 2, device="cpu", crop=None) -> torch.Tensor:
     """C3 family: smooth sine for x < 1/2, k constant Voronoi regions in x >= 1/2."""
     rng = SplitMix64(seed)
     sites, states = _draw_regions(rng, k, 3, [0.5, 0.0, 0.0], [1.0, 1.0, 1.0], with_coin=False)
     return _voronoi_state(3, [n, n, n], [0.0] * 3, [1.0] * 3, sites, states, R, device,
-                          smooth_mask_fn=lambda c: c[0] < 0.5)
+                          smooth_mask_fn=lambda c: c[0] < 0.5, crop=crop)
 
 
-def mixed_voronoi(dim: int, n: int, k: int, seed: int, R: int = 2, device="cpu") -> torch.Tensor:
+def mixed_voronoi(dim: int, n: int, k: int, seed: int, R: int = 2, device="cpu", crop=None) -> torch.Tensor:
     """C4/C5 family: k regions, each the smooth sine state (coin 1/2) or a random constant."""
     rng = SplitMix64(seed)
     sites, states = _draw_regions(rng, k, dim, [0.0] * dim, [1.0] * dim, with_coin=True)
-    return _voronoi_state(dim, [n] * dim, [0.0] * dim, [1.0] * dim, sites, states, R, device)
+    return _voronoi_state(dim, [n] * dim, [0.0] * dim, [1.0] * dim, sites, states, R, device, crop=crop)
 
 
 def constant_state(dim: int, n, rho=1.0, vel=None, p=1.0) -> torch.Tensor:
