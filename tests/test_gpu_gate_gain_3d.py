@@ -39,19 +39,21 @@ def _gated(kfvm, n, bc, tc=1):
 
 
 @pytest.mark.parametrize("tc,bound", [(0, 1.1), (1, 1.15)])
-def test_smooth_translation_3d_error_not_worse_than_fp64_weno(kfvm, tc, bound):
-    """32^3 sine translation (periodic) to t = 0.05: the gated mixed path's L1 density error against
+def test_smooth_translation_3d_gated_error_known_gap_within_15pct_of_fp64_weno(kfvm, tc, bound):
+    """A KNOWN GAP, recorded: at radius 3 in 3D the matched-L1 target (gated mixed path's L1 density
+    error within 1e-6 relative of the plain FP64 WENO-AO path's on smooth data) is NOT met.
+
+    32^3 sine translation (periodic) to t = 0.05: the gated mixed path's L1 density error against
     the exact solution, relative to the plain FP64 WENO-AO path's.  In 3D at radius 3 the shipped
     gate sends only part of the smooth cells (about a quarter here) to the linear reconstruction:
     its training labels come from radius-3 WENO-AO weights, which call much of an evolving 3D flow
     non-smooth, and its inputs see radius 2 plus a summary of the radius-3 shell.  A field that
     mixes linear and WENO-AO cells measures 8% (FP32-pipe contraction) / 11% (tensor-core
-    contraction, Riemann states within 1.4x the FP32 pipe's rounding on this data) above the
-    all-WENO error.  Neither the 2D gate's gain (a ~10x smaller error) nor the 1e-6 bar holds in this case;
-    the bound records that.  The cause is the linear operator: at radius 3 in 3D the linear S0
-    reconstruction with SSP-RK3 is not stable at CFL 0.4 (all cells linear: L1 7-10x the WENO-AO
-    error here, test_gpu_kxrcf.py), so linear cells in smooth regions lean on the WENO-AO cells
-    around them."""
+    contraction) above the all-WENO error; this test bounds that gap at 10% / 15%.  The cause is
+    the linear operator: at radius 3 in 3D the linear S0 reconstruction is not stable (von Neumann
+    symbol of the oracle's weights, which an independent 40-digit solve pins: max Re lambda Delta
+    = +7.5; all cells linear diverge, test_gpu_kxrcf.py), so linear cells in smooth regions lean
+    on the WENO-AO cells around them and cannot bring the 2D gate's ~10x gain."""
     n, t_end = 32, 0.05
     U0 = workloads.sine_3d(n)
     ex = workloads.sine_3d_exact_density(n, t_end)
