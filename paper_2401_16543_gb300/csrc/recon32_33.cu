@@ -360,24 +360,27 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
 // (hi + lo); B holds the weights split the same way (each output column scaled by a
 // power of two).  Three kind::f16 MMAs per k-step (hi.hi + hi.lo + lo.hi, FP32
 // accumulation in TMEM) carry ~22 bits, close to the FP32 contraction.
-//   pass 1: derivative values of every stencil, D1 = 8 blocks of 32 TMEM columns
-//           (stencil q's k-steps accumulate into columns 32 q ...), read back per
-//           cell -> beta_q -> WENO-AO coefficients (as in the CUDA-core kernel);
-//   pass 2: A rebuilt (the same deltas), each stencil's k-steps accumulating its 54
-//           face values in its own 64 TMEM columns (the derivative region is free by
-//           then); the WENO-AO blend with the cell's coefficients runs in float32 on
-//           the loaded values (folding the coefficients into A would push the products
-//           of small coefficients into FP16's subnormal range).
-// Tiles whose cells are all linear (gated modes) skip pass 1 and run the 8 k-steps
-// of S0 only.  The CTA is persistent (one per SM): B (138 KB, FP16 hi/lo) is
-// loaded into shared memory once; 512 threads build A chunks (cell r = t % 128,
-// quarter h = t / 128 of each 16-wide k-step) in a ring of 2 chunks of 2 k-steps, thread 0
-// issues the MMAs and commits each buffer back to its mbarrier (a hand-off through
-// per-buffer "full" mbarriers instead of the CTA barrier measured 10% slower).  The scale s of a
-// (cell, variable) is the power of two at or above the central cell's own scale
-// (rho~, sound speed, p~), so A stays O(1) (FP16 subnormals cost at most ~3e-8 of that
-// scale).  Every wait has an iteration limit; on expiry the kernel
-// raises the timeout flag and stops.
+//
+// Each chunk of A is built once per (tile, variable) and feeds two GEMMs: the
+// derivative values of its stencil (N = 32, Eq. 23 rows) and the face values of its
+// stencil (N = 64, Eq. 18 rows).  A stencil's accumulators occupy one of five TMEM
+// regions (face block at column 64 i, derivative block at 320 + 32 i); the stencils
+// are consumed in order as soon as their MMAs complete: beta_q (Eq. 22) -> the
+// unnormalised WENO weight w~_q = gamma_q / (beta'^2 + eps') (Eq. 24, beta' = beta / s^2,
+// eps' = eps / s^4, the same weights as gamma_q / (beta^2 + eps) after normalisation) ->
+// the WENO-AO coefficient of Eq. 19 times the stencil's face values, added to a running
+// blend (S0 first, so w~_0 is known for every later stencil); the blend is divided by
+// sum_q w~_q at the end.  The region is then handed back to the MMA-issuing thread.
+// Denominators are floored at 1e-30: stencils whose beta' is below 1e-15 (a relative
+// variation under the float32 resolution of the state) count as equally smooth.
+// Tiles whose cells are all linear (gated modes) run the 8 face k-steps of S0 only.
+// The CTA is persistent (one per SM): B (138 KB, FP16 hi/lo) is loaded into shared
+// memory once; 512 threads build A chunks (cell r = t % 128, quarter h = t / 128 of each
+// 16-wide k-step) in a ring of 2 chunks of 2 k-steps; thread 0 issues the MMAs and
+// commits each buffer back to its mbarrier.  The scale s of a (cell, variable) is the
+// power of two at or above the central cell's own scale (rho~, sound speed, p~), so A
+// stays O(1) (FP16 subnormals cost at most ~3e-8 of that scale).  Every wait has an
+// iteration limit; on expiry the kernel raises the timeout flag and stops.
 // ===========================================================================
 namespace tcg {
 
@@ -386,19 +389,26 @@ constexpr int KT = KS * 16;                // padded K = 368
 constexpr int TCT = 512;                   // threads per CTA: 4 per cell row (a quarter of each k-step)
 constexpr int KPC = 2;                     // MMA k-steps per ring chunk (one CTA barrier per chunk)
 constexpr int NB = 2;                      // A ring buffers
-constexpr int B1_BLOCK = 2048;             // pass-1 B block: 32 x 16 FP16, hi + lo
-constexpr int B2_BLOCK = 4096;             // pass-2 B block: 64 x 16 FP16, hi + lo
+constexpr int NREG = 5;                    // TMEM regions, one stencil's accumulators each
+constexpr int B1_BLOCK = 2048;             // derivative B block: 32 x 16 FP16, hi + lo
+constexpr int B2_BLOCK = 4096;             // face B block: 64 x 16 FP16, hi + lo
 constexpr int B1_BYTES = KS * B1_BLOCK;
 constexpr int B2_BYTES = KS * B2_BLOCK;
-constexpr int CS_FLOATS = NQ * 32 + 64;    // column scales (pass 1 per stencil, pass 2)
+constexpr int CS_FLOATS = NQ * 32 + 64;    // column scales (derivatives per stencil, faces)
 constexpr int B_BYTES = B1_BYTES + B2_BYTES + CS_FLOATS * 4;
 constexpr int A_KS = 8192;                 // one k-step of A: 128 x 16 FP16, hi + lo
 constexpr int A_BUF = KPC * A_KS;          // one ring chunk
 constexpr int WAIT_LIMIT = 1 << 22;
 
+// TMEM columns of region i: each block aligned to its own width
+__host__ __device__ constexpr uint32_t face_col(int i) { return 64u * (uint32_t)i; }
+__host__ __device__ constexpr uint32_t der_col(int i) { return 64u * NREG + 32u * (uint32_t)i; }
+static_assert(der_col(NREG) <= 512, "five regions of 96 TMEM columns");
+
 struct KMap {
   int kq[KS];       // stencil of each k-step
   int first[KS];    // 1 on the first k-step of a stencil
+  int last_of[NQ];  // last k-step of each stencil
   int off[KT];      // tile offset of each padded K column; kPad for padding
 };
 constexpr int kPad = 1 << 28;
@@ -421,10 +431,12 @@ constexpr KMap make_kmap() {
         m.off[kk] = kPad;
       }
     }
+    m.last_of[q] = kk / 16 - 1;
   }
   return m;
 }
 static_assert(make_kmap().kq[KS - 1] == NQ - 1, "23 k-steps");
+static_assert(make_kmap().last_of[0] == 7, "S0 takes 8 k-steps");
 __constant__ KMap c_kmap = make_kmap();
 
 // shared memory (bytes)
@@ -432,10 +444,10 @@ struct TSmem {
   static constexpr int b_off = 0;
   static constexpr int a_off = B_BYTES;                          // ring of NB A buffers
   static constexpr int tile_off = a_off + NB * A_BUF;            // (NV + 1) x SN floats
-  static constexpr int beta_off = tile_off + (NV + 1) * SN * 4;  // [128][NQ] floats
-  static constexpr int pack_off = beta_off + 128 * NQ * 4;       // gate parameters
+  static constexpr int pack_off = tile_off + (NV + 1) * SN * 4;  // gate parameters
   static constexpr int bar_off = (pack_off + (int)sizeof(gate::Pack<3>) + 15) / 16 * 16;
-  static constexpr int total = bar_off + 8 * (NB + 1) + 16;
+  static constexpr int nbar = NB + 2 * NREG + 1;                 // chunk_free, sten_done, reg_free, drain
+  static constexpr int total = bar_off + 8 * nbar + 16;
 };
 static_assert(TSmem::total <= 232448, "shared memory of one CTA");
 static_assert(128 * gate::Dims<3>::LDX * 2 + 128 * 4 <= NB * A_BUF, "gate staging fits in the A ring");
@@ -461,12 +473,13 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   unsigned char* As = tsm + TSmem::a_off;
   float* sm = reinterpret_cast<float*>(tsm + TSmem::tile_off);
   float* sp = sm + NV * SN;
-  float* bpart = reinterpret_cast<float*>(tsm + TSmem::beta_off);
   const float* cs1 = reinterpret_cast<const float*>(Bs + B1_BYTES + B2_BYTES);
   const float* cs2 = cs1 + NQ * 32;
   uint64_t* chunk_free = reinterpret_cast<uint64_t*>(tsm + TSmem::bar_off);
-  uint64_t* pass_done = chunk_free + NB;
-  uint32_t* tbase_s = reinterpret_cast<uint32_t*>(pass_done + 1);
+  uint64_t* sten_done = chunk_free + NB;  // one commit per stencil occupying region i
+  uint64_t* reg_free = sten_done + NREG;  // every warp has read region i's occupant
+  uint64_t* drain = reg_free + NREG;      // exit after a failed wait
+  uint32_t* tbase_s = reinterpret_cast<uint32_t*>(drain + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r = tid & 127, h = tid >> 7;
@@ -480,7 +493,11 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   if (mode == 2) gate::load_pack<3>(gpack, P);
   if (tid == 0) {
     for (int i = 0; i < NB; ++i) tc::mbar_init(chunk_free + i, 1);
-    tc::mbar_init(pass_done, 1);
+    for (int i = 0; i < NREG; ++i) {
+      tc::mbar_init(sten_done + i, 1);
+      tc::mbar_init(reg_free + i, TCT / 32);
+    }
+    tc::mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tc::tmem_alloc(tbase_s, 512);
@@ -493,66 +510,16 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   const uint32_t id32 = tc::idesc_f16_f32(128, 32), id64 = tc::idesc_f16_f32(128, 64);
   const uint32_t a_addr = tc::smem_addr(As), b_addr = tc::smem_addr(Bs);
 
-  uint32_t it = 0, pd_parity = 0;
+  uint32_t it = 0;                // A ring chunks used so far
+  uint32_t sd_ph = 0;             // next parity of each sten_done barrier (bit i)
+  uint32_t rf_ph = 0, rf_used = 0;  // issuer: next parity of each reg_free barrier, regions used once
   bool ok = true;
-
-  // one ring chunk of nj (<= KPC) k-steps starting at j0: every thread writes its 4 columns (hi, lo)
-  // of row r per k-step, value(j, e) giving column 16 j + 4 h + e; after the CTA barrier thread 0
-  // issues three MMAs per k-step as mma_of(j) describes and commits the chunk's buffer
-  auto kchunk = [&](int j0, int nj, auto&& value, auto&& mma_of) {
-    const int buf = (int)(it % NB);
-    const uint32_t use = it / NB;
-    if (use > 0 && !tc::mbar_wait(chunk_free + buf, (use - 1) & 1u, WAIT_LIMIT)) ok = false;
-    unsigned char* base = As + buf * A_BUF;
-    const int ob = tile_byte(r, 4 * h);
-#pragma unroll
-    for (int jj = 0; jj < KPC; ++jj) {
-      if (jj < nj) {
-        float x[4], rs[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          x[e] = value(j0 + jj, e);
-          rs[e] = x[e] - __half2float(__float2half_rn(x[e]));
-        }
-        uint2 hi, lo;
-        hi.x = pack_half2(x[0], x[1]);
-        hi.y = pack_half2(x[2], x[3]);
-        lo.x = pack_half2(rs[0], rs[1]);
-        lo.y = pack_half2(rs[2], rs[3]);
-        *reinterpret_cast<uint2*>(base + jj * A_KS + ob) = hi;
-        *reinterpret_cast<uint2*>(base + jj * A_KS + A_KS / 2 + ob) = lo;
-      }
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      for (int jj = 0; jj < nj; ++jj) {
-        uint32_t d_col, idesc, b_hi, b_lo, acc;
-        mma_of(j0 + jj, d_col, idesc, b_hi, b_lo, acc);
-        const uint32_t ab = a_addr + buf * A_BUF + jj * A_KS;
-        const uint64_t ahi = tc::smem_desc(ab, 128, 256), alo = tc::smem_desc(ab + A_KS / 2, 128, 256);
-        const uint64_t bhi = tc::smem_desc(b_hi, 128, 256), blo = tc::smem_desc(b_lo, 128, 256);
-        tc::mma_f16(tbase + d_col, ahi, bhi, idesc, acc);
-        tc::mma_f16(tbase + d_col, ahi, blo, idesc, 1u);
-        tc::mma_f16(tbase + d_col, alo, bhi, idesc, 1u);
-      }
-      tc::commit(chunk_free + buf);
-    }
-    ++it;
-  };
-  auto finish_pass = [&]() {
-    if (tid == 0) tc::commit(pass_done);
-    if (!tc::mbar_wait(pass_done, pd_parity, WAIT_LIMIT)) ok = false;
-    pd_parity ^= 1u;
-    tc::fence_after_sync();
-  };
 
   // test hook of the bounded waits: wait on a phase that nothing completes (an mbarrier no thread
   // arrives on), give up after a short limit, raise the timeout flag and do no work
   if (timeout_probe) {
     bool got = true;
-    if (tid == 0) got = tc::mbar_wait(pass_done, pd_parity, 1 << 10);  // phase 0 of a fresh barrier
+    if (tid == 0) got = tc::mbar_wait(reg_free, 0u, 1 << 10);  // phase 0 of a fresh barrier
     ok = __syncthreads_and(got) != 0;
   }
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -575,7 +542,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
     const long long fcell = active ? ((long long)l * a.n[1] + y) * a.n[0] + x : 0;
 
     // which rows are linear (gated modes); the gate's staging lives in the A ring (free here:
-    // the previous tile's last pass has completed)
+    // every MMA of the previous tile has completed)
     bool smooth = false;
     if (mode == 2) {
       using DM = gate::Dims<3>;
@@ -604,128 +571,148 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
     }
     const bool weno_row = active && (mode == 0 || (mode == 2 && !smooth) || (mode == 3 && !gate_mask[cell]));
     const bool weno_tile = __syncthreads_or(weno_row) != 0;
+    const int ks_end = weno_tile ? KS : c_kmap.last_of[0] + 1;
+    const int nq_used = weno_tile ? NQ : 1;
 
 #pragma unroll 1
     for (int v = 0; v < NV && ok; ++v) {
       const Ref ref(sm, c, v, gm1);
-      auto delta_at = [&](int kk) -> float {
-        const int o = c_kmap.off[kk];
-        return (active && o != kPad) ? ref.delta(sm, c + o) : 0.0f;
-      };
       // s = power of two at or above the central cell's scale of this variable
       const float pc = sp[c];
       const float scale = v == 0 ? ref.uc[0] : (v == NV - 1 ? pc : sqrtf(fmaxf(a.gammaf * pc * ref.irt, 0.0f)));
       int ex = 0;
       if (scale > 0.0f && scale < 3.0e38f) frexpf(scale, &ex);
       const float inv_s = ldexpf(1.0f, -ex), sc = ldexpf(1.0f, ex);
+      const float eps_s = fminf(ldexpf(a.epsf, -4 * ex), 1.0e30f);  // eps / s^4
 
-      float coef[NQ];
-      coef[0] = 1.0f;
+      float acc[16];
 #pragma unroll
-      for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
-      if (weno_tile) {
-        // ---- pass 1: derivative values of every stencil ----
-        auto value1 = [&](int j, int e) { return delta_at(16 * j + 4 * h + e) * inv_s; };
-        auto mma1 = [&](int j, uint32_t& d_col, uint32_t& idesc, uint32_t& b_hi, uint32_t& b_lo, uint32_t& acc) {
-          d_col = 32u * c_kmap.kq[j];
-          idesc = id32;
-          b_hi = b_addr + j * B1_BLOCK;
-          b_lo = b_hi + B1_BLOCK / 2;
-          acc = c_kmap.first[j] ? 0u : 1u;
-        };
-#pragma unroll 1
-        for (int j0 = 0; j0 < KS; j0 += KPC) kchunk(j0, KS - j0 < KPC ? KS - j0 : KPC, value1, mma1);
-        finish_pass();
-        // beta'_q = sum_m (D1 * column scale)^2 for this quarter's two stencils
-#pragma unroll 1
-        for (int qq = 0; qq < 2; ++qq) {
-          const int q = 2 * h + qq;
+      for (int m = 0; m < 16; ++m) acc[m] = 0.0f;
+      float wsum = 0.0f, w0g = 0.0f;  // sum of w~_q; w~_0 / gamma_0
+      int nc = 0;                     // stencils consumed
+
+      // stencil q's accumulators -> running WENO-AO blend of this thread's 16 face columns; the
+      // region goes back to the issuer once every warp has read it
+      auto consume = [&](int q) {
+        const int i = q % NREG;
+        if (!tc::mbar_wait(sten_done + i, (sd_ph >> i) & 1u, WAIT_LIMIT)) ok = false;
+        sd_ph ^= 1u << i;
+        tc::fence_after_sync();
+        float cq = q == 0 ? 1.0f : 0.0f;  // linear rows: S0 alone
+        if (weno_tile) {
           float d0[16], d1[16];
-          tc::tmem_ld16(tbase + lane_base + 32u * q, d0);
-          tc::tmem_ld16(tbase + lane_base + 32u * q + 16u, d1);
-          float bq = 0.0f;
+          tc::tmem_ld16(tbase + lane_base + der_col(i), d0);
+          tc::tmem_ld16(tbase + lane_base + der_col(i) + 16u, d1);
+          if (weno_row) {
+            float bq = 0.0f;
 #pragma unroll
-          for (int m = 0; m < 16; ++m) {
-            const float dm = d0[m] * cs1[q * 32 + m];
-            bq = fmaf(dm, dm, bq);
-          }
-#pragma unroll
-          for (int m = 16; m < M; ++m) {
-            const float dm = d1[m - 16] * cs1[q * 32 + m];
-            bq = fmaf(dm, dm, bq);
-          }
-          bpart[r * NQ + q] = bq;
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        if (weno_row) {
-          // nonlinear weights (Eq. 24, scaled form; the common factor 1/s^2 of beta' cancels in the
-          // ratios, eps/beta_max^2 uses the true beta_max = beta'_max s^2) and WENO-AO coefficients
-          float beta[NQ], bmax = 0.0f;
-#pragma unroll
-          for (int q = 0; q < NQ; ++q) {
-            beta[q] = bpart[r * NQ + q];
-            bmax = fmaxf(bmax, beta[q]);
-          }
-          if (bmax > 0.0f) {
-            const float ib = __frcp_rn(bmax);
-            const float is2 = inv_s * inv_s;
-            const float e = fmaxf(a.epsf * (ib * is2) * (ib * is2), 1e-30f);
-            float om[NQ], sum = 0.0f;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-              const float bq = beta[q] * ib;
-              om[q] = __fdividef((float)linear_weight<3>(q), fmaf(bq, bq, e));
-              sum += om[q];
+            for (int m = 0; m < 16; ++m) {
+              const float dm = d0[m] * cs1[q * 32 + m];
+              bq = fmaf(dm, dm, bq);
             }
-            const float inv = __frcp_rn(sum);
-            const float w0 = om[0] * inv;
-            coef[0] = w0 / (float)linear_weight<3>(0);
 #pragma unroll
-            for (int q = 1; q < NQ; ++q)
-              coef[q] = fmaf(-w0, (float)(linear_weight<3>(q) / linear_weight<3>(0)), om[q] * inv);
+            for (int m = 16; m < M; ++m) {
+              const float dm = d1[m - 16] * cs1[q * 32 + m];
+              bq = fmaf(dm, dm, bq);
+            }
+            float gq = (float)linear_weight<3>(0);
+#pragma unroll
+            for (int qq = 1; qq < NQ; ++qq) gq = (q == qq) ? (float)linear_weight<3>(qq) : gq;
+            const float wq = __fdividef(gq, fmaxf(fmaf(bq, bq, eps_s), 1.0e-30f));
+            wsum += wq;
+            if (q == 0) {
+              w0g = wq * (float)(1.0 / linear_weight<3>(0));
+              cq = w0g;
+            } else {
+              cq = fmaf(-w0g, gq, wq);  // w~_q - w~_0 gamma_q / gamma_0
+            }
           }
         }
-      }
-      // ---- pass 2: blended face values (S0 only on an all-linear tile) ----
-      const int ks_end = weno_tile ? KS : 8;
-      // pass 2: each stencil's face values into its own 64 TMEM columns (the derivative columns have
-      // been read: the region is free), the WENO-AO blend in float32 afterwards.  Folding the
-      // coefficients into A instead would push the small ones' products into FP16's subnormal range.
-      auto value2 = [&](int j, int e) { return delta_at(16 * j + 4 * h + e) * inv_s; };
-      auto mma2 = [&](int j, uint32_t& d_col, uint32_t& idesc, uint32_t& b_hi, uint32_t& b_lo, uint32_t& acc) {
-        d_col = 64u * c_kmap.kq[j];
-        idesc = id64;
-        b_hi = b_addr + B1_BYTES + j * B2_BLOCK;
-        b_lo = b_hi + B2_BLOCK / 2;
-        acc = c_kmap.first[j] ? 0u : 1u;
+        float f[16];
+        tc::tmem_ld16(tbase + lane_base + face_col(i) + 16u * h, f);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) acc[m] = fmaf(cq, f[m], acc[m]);
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(reg_free + i);
       };
+
 #pragma unroll 1
-      for (int j0 = 0; j0 < ks_end; j0 += KPC) kchunk(j0, ks_end - j0 < KPC ? ks_end - j0 : KPC, value2, mma2);
-      finish_pass();
-      {
-        float out[16];
+      for (int j0 = 0; j0 < ks_end; j0 += KPC) {
+        const int nj = ks_end - j0 < KPC ? ks_end - j0 : KPC;
+        // build the chunk: every thread writes its 4 columns (hi, lo) of row r per k-step
+        const int buf = (int)(it % NB);
+        const uint32_t use = it / NB;
+        if (use > 0 && !tc::mbar_wait(chunk_free + buf, (use - 1) & 1u, WAIT_LIMIT)) ok = false;
+        unsigned char* base = As + buf * A_BUF;
+        const int ob = tile_byte(r, 4 * h);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) out[m] = 0.0f;
-#pragma unroll 1
-        for (int q = 0; q < (weno_tile ? NQ : 1); ++q) {
-          float d0[16];
-          tc::tmem_ld16(tbase + lane_base + 64u * q + 16u * h, d0);
-          float cq = coef[0];
+        for (int jj = 0; jj < KPC; ++jj) {
+          if (jj < nj) {
+            float xv[4], rs[4];
 #pragma unroll
-          for (int qq = 1; qq < NQ; ++qq) cq = (q == qq) ? coef[qq] : cq;
-#pragma unroll
-          for (int m = 0; m < 16; ++m) out[m] = fmaf(cq, d0[m], out[m]);
-        }
-        if (active) {
-#pragma unroll
-          for (int m = 0; m < 16; ++m) {
-            const int sp_ = 16 * h + m;
-            if (sp_ < F) *slot(faces, ncell_f, fcell, sp_, v) = out[m] * cs2[sp_] * sc;
+            for (int e = 0; e < 4; ++e) {
+              const int o = c_kmap.off[16 * (j0 + jj) + 4 * h + e];
+              xv[e] = (active && o != kPad) ? ref.delta(sm, c + o) * inv_s : 0.0f;
+              rs[e] = xv[e] - __half2float(__float2half_rn(xv[e]));
+            }
+            uint2 hi, lo;
+            hi.x = pack_half2(xv[0], xv[1]);
+            hi.y = pack_half2(xv[2], xv[3]);
+            lo.x = pack_half2(rs[0], rs[1]);
+            lo.y = pack_half2(rs[2], rs[3]);
+            *reinterpret_cast<uint2*>(base + jj * A_KS + ob) = hi;
+            *reinterpret_cast<uint2*>(base + jj * A_KS + A_KS / 2 + ob) = lo;
           }
         }
+        tc::fence_proxy_async();
+        __syncthreads();
+        // stencils whose MMAs were issued in earlier chunks, before this chunk's MMAs (which may
+        // need their regions)
+        while (nc < nq_used && c_kmap.last_of[nc] < j0) consume(nc++);
+        if (tid == 0) {
+          tc::fence_after_sync();
+          for (int jj = 0; jj < nj; ++jj) {
+            const int j = j0 + jj, q = c_kmap.kq[j], i = q % NREG;
+            if (c_kmap.first[j]) {
+              if ((rf_used >> i) & 1u) {
+                if (!tc::mbar_wait(reg_free + i, (rf_ph >> i) & 1u, WAIT_LIMIT)) ok = false;
+                rf_ph ^= 1u << i;
+                tc::fence_after_sync();
+              }
+              rf_used |= 1u << i;
+            }
+            const uint32_t acc0 = c_kmap.first[j] ? 0u : 1u;
+            const uint32_t ab = a_addr + buf * A_BUF + jj * A_KS;
+            const uint64_t ahi = tc::smem_desc(ab, 128, 256), alo = tc::smem_desc(ab + A_KS / 2, 128, 256);
+            if (weno_tile) {
+              const uint32_t bh = b_addr + j * B1_BLOCK;
+              const uint64_t bhi = tc::smem_desc(bh, 128, 256), blo = tc::smem_desc(bh + B1_BLOCK / 2, 128, 256);
+              tc::mma_f16(tbase + der_col(i), ahi, bhi, id32, acc0);
+              tc::mma_f16(tbase + der_col(i), ahi, blo, id32, 1u);
+              tc::mma_f16(tbase + der_col(i), alo, bhi, id32, 1u);
+            }
+            const uint32_t bh = b_addr + B1_BYTES + j * B2_BLOCK;
+            const uint64_t bhi = tc::smem_desc(bh, 128, 256), blo = tc::smem_desc(bh + B2_BLOCK / 2, 128, 256);
+            tc::mma_f16(tbase + face_col(i), ahi, bhi, id64, acc0);
+            tc::mma_f16(tbase + face_col(i), ahi, blo, id64, 1u);
+            tc::mma_f16(tbase + face_col(i), alo, bhi, id64, 1u);
+            if (j == c_kmap.last_of[q]) tc::commit(sten_done + i);
+          }
+          tc::commit(chunk_free + buf);
+        }
+        ++it;
       }
-      tc::fence_before_sync();
+      while (nc < nq_used) consume(nc++);
+      // blended face values / sum_q w~_q, back in the variable's units
+      const float inv_w = weno_row ? __frcp_rn(wsum) : 1.0f;
+      if (active) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int sp_ = 16 * h + m;
+          if (sp_ < F) *slot(faces, ncell_f, fcell, sp_, v) = acc[m] * inv_w * cs2[sp_] * sc;
+        }
+      }
       ok = __syncthreads_and(ok) != 0;
     }
     if (!ok) break;
@@ -737,15 +724,14 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   if (!ok) {
     if (tid == 0) raise_flag(a.status, kFlagTimeout);
     // let whatever is still in flight finish (bounded) before the TMEM goes back
-    if (tid == 0) tc::commit(pass_done);
-    tc::mbar_wait(pass_done, pd_parity, WAIT_LIMIT);
+    if (tid == 0) tc::commit(drain);
+    tc::mbar_wait(drain, 0u, WAIT_LIMIT);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
-
 }  // namespace tcg
 }  // namespace r33
 

@@ -54,6 +54,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
 }
 
+// one arrival on an mbarrier (the arrival state is not needed)
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+
 // wait for the completion of phase `parity` of an mbarrier; false after `limit` polls
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int limit) {
   uint32_t done = 0;
