@@ -350,6 +350,115 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
   y[cell] = worst >= thresh ? 1.0f : 0.0f;
 }
 
+// Tail of one cell shared by its four threads of the tensor-core kernel (quarter h owns the face
+// points 16 h ... 16 h + 15): the same arithmetic as r32::write_states -- central pressure (float64
+// where E/p shows cancellation), positivity limiter (Sec. 4) on the reconstructed dW = dwget(s, v),
+// float32 primitive Riemann states -- with the limiter's theta_rho and theta_p, minima over all 54
+// points, combined through shared memory (xch: 2 x 4 x 128 floats).  Every thread of the CTA calls
+// it (it holds two CTA barriers); inactive rows only take part in the barriers.
+template <class DW>
+__device__ __forceinline__ void write_states_split(const GridArgs& a, const float* __restrict__ sm,
+                                                   const float* __restrict__ sp, int c, const double* __restrict__ U,
+                                                   long long ncell, long long cell, long long fcell, long long ncell_f,
+                                                   float* faces, bool active, int r, int h, float* xch, DW dwget) {
+  const int s_lo = 16 * h, s_hi = s_lo + 16 < F ? s_lo + 16 : F;
+  const float gm1 = a.gammaf - 1.0f;
+  float uc[NV], ut[3], kin, irt;
+  float pt = 0.0f, rt = 1.0f, cq = 0.0f, th = 1.0f, thp = 1.0f;
+  float p_min = 0.0f;
+  if (active) {
+    r32::cell_ref<3, 3>(sm, c, uc, ut, kin, irt);
+    // central pressure: float32 where E/p < 8, else recovered in float64 from the state
+    pt = sp[c];
+    if (!(pt > 0.125f * uc[NV - 1])) {
+      double m2 = 0.0, u8[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) u8[v] = U[v * ncell + cell];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) m2 = fma(u8[1 + k], u8[1 + k], m2);
+      const double p8 = (a.gamma - 1.0) * fma(-0.5 * m2, recip64(u8[0]), u8[NV - 1]);
+      pt = (float)p8;
+      if (!(u8[0] > 0.0) || !(p8 > 0.0)) raise_flag(a.status, kFlagNonphysical);
+    }
+    rt = uc[0];
+    cq = 0.5f * gm1 * rt * rt;  // (gamma-1) rho~^2 / 2
+    if (a.positivity) {
+      float rmax = -3.0e38f, rmin = 3.0e38f, pmin = 3.0e38f;
+#pragma unroll
+      for (int k = -1; k <= 1; ++k)
+#pragma unroll
+        for (int j = -1; j <= 1; ++j)
+#pragma unroll
+          for (int i = -1; i <= 1; ++i) {
+            const int o = c + i + T::SX * (j + T::SY * k);
+            rmax = fmaxf(rmax, sm[o]);
+            rmin = fminf(rmin, sm[o]);
+            pmin = fminf(pmin, sp[o]);
+          }
+      const float rho_max = rmax * a.hi_f, rho_min = rmin * a.lo_f;
+      p_min = pmin * a.lo_f;
+      for (int s = s_lo; s < s_hi; ++s) {
+        const float rs = rt + dwget(s, 0);
+        if (rs < rho_min) th = fminf(th, (rt - rho_min) / (rt - rs));
+        if (rs > rho_max) th = fminf(th, (rho_max - rt) / (rs - rt));
+      }
+    }
+  }
+  xch[h * 128 + r] = th;
+  __syncthreads();
+  th = fminf(fminf(xch[r], xch[128 + r]), fminf(xch[256 + r], xch[384 + r]));
+  if (active && a.positivity) {
+    // p(theta) >= p_min  <=>  (pt + theta dpi - p_min) (rt + theta drho) >= cq theta^2 |du|^2
+    auto admissible = [&](float t, float dr, float dp, float du2) {
+      const float rr = fmaf(t, dr, rt);
+      return rr > 0.0f && (fmaf(t, dp, pt) - p_min) * rr >= cq * t * t * du2;
+    };
+#pragma unroll 1
+    for (int s = s_lo; s < s_hi; ++s) {
+      const float dr = th * dwget(s, 0);
+      const float dp = th * dwget(s, NV - 1);
+      float du2 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float du = th * dwget(s, 1 + k);
+        du2 = fmaf(du, du, du2);
+      }
+      if (admissible(1.0f, dr, dp, du2)) continue;
+      float lo = 0.0f, hi = 1.0f;
+#pragma unroll 1
+      for (int it = 0; it < 40; ++it) {
+        const float mid = 0.5f * (lo + hi);
+        if (admissible(mid, dr, dp, du2)) lo = mid; else hi = mid;
+      }
+      thp = fminf(thp, lo);
+    }
+  }
+  xch[512 + h * 128 + r] = thp;
+  __syncthreads();
+  thp = fminf(fminf(xch[512 + r], xch[640 + r]), fminf(xch[768 + r], xch[896 + r]));
+  if (!active) return;
+  const float scl = th * thp;
+  float4* out4 = reinterpret_cast<float4*>(faces);
+#pragma unroll 1
+  for (int s = s_lo; s < s_hi; ++s) {
+    const float dr = scl * dwget(s, 0);
+    const float rs = rt + dr;
+    const float irs = __frcp_rn(rs);
+    float du2 = 0.0f, uo[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float du = scl * dwget(s, 1 + k);
+      du2 = fmaf(du, du, du2);
+      uo[k] = fmaf(rt * du, irs, ut[k]);
+    }
+    const float dp = scl * dwget(s, NV - 1);
+    const float ps = fmaf(-cq * du2, irs, pt + dp);
+    // float32 layout: [s][cell] float4 (rho, u, v, p), then the plane [s][cell] of w
+    out4[(long long)s * ncell_f + fcell] = make_float4(rs, uo[0], uo[1], ps);
+    faces[4LL * F * ncell_f + (long long)s * ncell_f + fcell] = uo[2];
+  }
+}
+
 // ===========================================================================
 // Tensor-core variant (tcgen05): the contraction as a GEMM per (tile of 128 cells, variable).
 //
@@ -600,9 +709,10 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
         tc::fence_after_sync();
         float cq = q == 0 ? 1.0f : 0.0f;  // linear rows: S0 alone
         if (weno_tile) {
-          float d0[16], d1[16];
+          static_assert(M > 16 && M <= 20, "19 derivative columns: 16 + 4 loaded");
+          float d0[16], d1[4];
           tc::tmem_ld16(tbase + lane_base + der_col(i), d0);
-          tc::tmem_ld16(tbase + lane_base + der_col(i) + 16u, d1);
+          tc::tmem_ld4(tbase + lane_base + der_col(i) + 16u, d1);
           if (weno_row) {
             float bq = 0.0f;
 #pragma unroll
@@ -716,10 +826,11 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
       ok = __syncthreads_and(ok) != 0;
     }
     if (!ok) break;
-    __syncthreads();  // every dW slot of the tile written
-    if (h == 0 && active)
-      r32::write_states<3, 3>(a, sm, sp, c, U, (long long)a.n[0] * a.n[1] * a.n[2], cell, fcell, ncell_f, faces,
-                              [&](int s_, int v_) { return *slot(faces, ncell_f, fcell, s_, v_); });
+    // the tail, four threads per cell: each reads back only the dW slots it wrote itself; the A ring
+    // (every MMA consumed) holds the limiter's exchange
+    write_states_split(a, sm, sp, c, U, (long long)a.n[0] * a.n[1] * a.n[2], cell, fcell, ncell_f, faces, active, r,
+                       h, reinterpret_cast<float*>(As),
+                       [&](int s_, int v_) { return *slot(faces, ncell_f, fcell, s_, v_); });
   }
   if (!ok) {
     if (tid == 0) raise_flag(a.status, kFlagTimeout);
