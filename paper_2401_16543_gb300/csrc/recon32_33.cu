@@ -470,10 +470,10 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
 // power of two).  Three kind::f16 MMAs per k-step (hi.hi + hi.lo + lo.hi, FP32
 // accumulation in TMEM) carry ~22 bits, close to the FP32 contraction.
 //
-// Each chunk of A is built once per (tile, variable) and feeds two GEMMs: the
-// derivative values of its stencil (N = 32, Eq. 23 rows) and the face values of its
-// stencil (N = 64, Eq. 18 rows).  A stencil's accumulators occupy one of five TMEM
-// regions (face block at column 64 i, derivative block at 320 + 32 i); the stencils
+// Each chunk of A is built once per (tile, variable) and feeds one GEMM per product
+// with N = 96 columns: the 32 derivative columns of its stencil (Eq. 23 rows, 19 used)
+// and the 64 face columns (Eq. 18 rows, 54 used), one B block per k-step.  A stencil's
+// accumulators occupy one of four TMEM regions (columns 128 i ... 128 i + 95); the stencils
 // are consumed in order as soon as their MMAs complete: beta_q (Eq. 22) -> the
 // unnormalised WENO weight w~_q = gamma_q / (beta'^2 + eps') (Eq. 24, beta' = beta / s^2,
 // eps' = eps / s^4, the same weights as gamma_q / (beta^2 + eps) after normalisation) ->
@@ -485,8 +485,9 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
 // Tiles whose cells are all linear (gated modes) run the 8 face k-steps of S0 only.
 // The CTA is persistent (one per SM): B (138 KB, FP16 hi/lo) is loaded into shared
 // memory once; 512 threads build A chunks (cell r = t % 128, quarter h = t / 128 of each
-// 16-wide k-step) in a ring of 2 chunks of 2 k-steps; thread 0 issues the MMAs and
-// commits each buffer back to its mbarrier.  The scale s of a (cell, variable) is the
+// 16-wide k-step) in a ring of 2 chunks of 2 k-steps.  Each warp signals a written chunk
+// on the chunk's "full" mbarrier (no CTA-wide barrier: only the issuer waits for every
+// warp); thread 0 issues the MMAs and commits the buffer to its "free" mbarrier.  The scale s of a (cell, variable) is the
 // power of two at or above the central cell's own scale (rho~, sound speed, p~), so A
 // stays O(1) (FP16 subnormals cost at most ~3e-8 of that scale).  Every wait has an
 // iteration limit; on expiry the kernel raises the timeout flag and stops.
@@ -498,21 +499,20 @@ constexpr int KT = KS * 16;                // padded K = 368
 constexpr int TCT = 512;                   // threads per CTA: 4 per cell row (a quarter of each k-step)
 constexpr int KPC = 2;                     // MMA k-steps per ring chunk (one CTA barrier per chunk)
 constexpr int NB = 2;                      // A ring buffers
-constexpr int NREG = 5;                    // TMEM regions, one stencil's accumulators each
-constexpr int B1_BLOCK = 2048;             // derivative B block: 32 x 16 FP16, hi + lo
-constexpr int B2_BLOCK = 4096;             // face B block: 64 x 16 FP16, hi + lo
-constexpr int B1_BYTES = KS * B1_BLOCK;
-constexpr int B2_BYTES = KS * B2_BLOCK;
+constexpr int NREG = 4;                    // TMEM regions, one stencil's accumulators each
+constexpr int NOUT = 96;                   // MMA columns per k-step: 32 derivative + 64 face values
+constexpr int BB_BLOCK = NOUT * 16 * 2 * 2;  // B block of one k-step: 96 x 16 FP16, hi + lo
+constexpr int BB_BYTES = KS * BB_BLOCK;
 constexpr int CS_FLOATS = NQ * 32 + 64;    // column scales (derivatives per stencil, faces)
-constexpr int B_BYTES = B1_BYTES + B2_BYTES + CS_FLOATS * 4;
+constexpr int B_BYTES = BB_BYTES + CS_FLOATS * 4;
 constexpr int A_KS = 8192;                 // one k-step of A: 128 x 16 FP16, hi + lo
 constexpr int A_BUF = KPC * A_KS;          // one ring chunk
 constexpr int WAIT_LIMIT = 1 << 22;
 
-// TMEM columns of region i: each block aligned to its own width
-__host__ __device__ constexpr uint32_t face_col(int i) { return 64u * (uint32_t)i; }
-__host__ __device__ constexpr uint32_t der_col(int i) { return 64u * NREG + 32u * (uint32_t)i; }
-static_assert(der_col(NREG) <= 512, "five regions of 96 TMEM columns");
+// TMEM columns of region i (128 apart): the 32 derivative columns, then the 64 face columns
+__host__ __device__ constexpr uint32_t der_col(int i) { return 128u * (uint32_t)i; }
+__host__ __device__ constexpr uint32_t face_col(int i) { return 128u * (uint32_t)i + 32u; }
+static_assert(der_col(NREG - 1) + NOUT <= 512, "four regions of 96 TMEM columns");
 
 struct KMap {
   int kq[KS];       // stencil of each k-step
@@ -555,7 +555,7 @@ struct TSmem {
   static constexpr int tile_off = a_off + NB * A_BUF;            // (NV + 1) x SN floats
   static constexpr int pack_off = tile_off + (NV + 1) * SN * 4;  // gate parameters
   static constexpr int bar_off = (pack_off + (int)sizeof(gate::Pack<3>) + 15) / 16 * 16;
-  static constexpr int nbar = NB + 2 * NREG + 1;                 // chunk_free, sten_done, reg_free, drain
+  static constexpr int nbar = 2 * NB + 2 * NREG + 1;  // chunk_full, chunk_free, sten_done, reg_free, drain
   static constexpr int total = bar_off + 8 * nbar + 16;
 };
 static_assert(TSmem::total <= 232448, "shared memory of one CTA");
@@ -582,9 +582,10 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   unsigned char* As = tsm + TSmem::a_off;
   float* sm = reinterpret_cast<float*>(tsm + TSmem::tile_off);
   float* sp = sm + NV * SN;
-  const float* cs1 = reinterpret_cast<const float*>(Bs + B1_BYTES + B2_BYTES);
+  const float* cs1 = reinterpret_cast<const float*>(Bs + BB_BYTES);
   const float* cs2 = cs1 + NQ * 32;
-  uint64_t* chunk_free = reinterpret_cast<uint64_t*>(tsm + TSmem::bar_off);
+  uint64_t* chunk_full = reinterpret_cast<uint64_t*>(tsm + TSmem::bar_off);  // every warp wrote its rows
+  uint64_t* chunk_free = chunk_full + NB;  // the chunk's MMAs have completed
   uint64_t* sten_done = chunk_free + NB;  // one commit per stencil occupying region i
   uint64_t* reg_free = sten_done + NREG;  // every warp has read region i's occupant
   uint64_t* drain = reg_free + NREG;      // exit after a failed wait
@@ -601,7 +602,10 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   gate::Pack<3>* P = reinterpret_cast<gate::Pack<3>*>(tsm + TSmem::pack_off);
   if (mode == 2) gate::load_pack<3>(gpack, P);
   if (tid == 0) {
-    for (int i = 0; i < NB; ++i) tc::mbar_init(chunk_free + i, 1);
+    for (int i = 0; i < NB; ++i) {
+      tc::mbar_init(chunk_full + i, TCT / 32);
+      tc::mbar_init(chunk_free + i, 1);
+    }
     for (int i = 0; i < NREG; ++i) {
       tc::mbar_init(sten_done + i, 1);
       tc::mbar_init(reg_free + i, TCT / 32);
@@ -616,7 +620,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   tc::fence_after_sync();
   const uint32_t tbase = *tbase_s;
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-  const uint32_t id32 = tc::idesc_f16_f32(128, 32), id64 = tc::idesc_f16_f32(128, 64);
+  const uint32_t id96 = tc::idesc_f16_f32(128, NOUT);
   const uint32_t a_addr = tc::smem_addr(As), b_addr = tc::smem_addr(Bs);
 
   uint32_t it = 0;                // A ring chunks used so far
@@ -775,12 +779,15 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
             *reinterpret_cast<uint2*>(base + jj * A_KS + A_KS / 2 + ob) = lo;
           }
         }
+        // hand the chunk to the issuing thread: no CTA barrier, only the issuer waits for all warps
         tc::fence_proxy_async();
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(chunk_full + buf);
         // stencils whose MMAs were issued in earlier chunks, before this chunk's MMAs (which may
         // need their regions)
         while (nc < nq_used && c_kmap.last_of[nc] < j0) consume(nc++);
         if (tid == 0) {
+          if (!tc::mbar_wait(chunk_full + buf, use & 1u, WAIT_LIMIT)) ok = false;
           tc::fence_after_sync();
           for (int jj = 0; jj < nj; ++jj) {
             const int j = j0 + jj, q = c_kmap.kq[j], i = q % NREG;
@@ -792,21 +799,16 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
               }
               rf_used |= 1u << i;
             }
+            // derivative and face columns of stencil q in one N = 96 MMA per product (all-linear
+            // tiles compute the derivative columns too and ignore them)
             const uint32_t acc0 = c_kmap.first[j] ? 0u : 1u;
             const uint32_t ab = a_addr + buf * A_BUF + jj * A_KS;
             const uint64_t ahi = tc::smem_desc(ab, 128, 256), alo = tc::smem_desc(ab + A_KS / 2, 128, 256);
-            if (weno_tile) {
-              const uint32_t bh = b_addr + j * B1_BLOCK;
-              const uint64_t bhi = tc::smem_desc(bh, 128, 256), blo = tc::smem_desc(bh + B1_BLOCK / 2, 128, 256);
-              tc::mma_f16(tbase + der_col(i), ahi, bhi, id32, acc0);
-              tc::mma_f16(tbase + der_col(i), ahi, blo, id32, 1u);
-              tc::mma_f16(tbase + der_col(i), alo, bhi, id32, 1u);
-            }
-            const uint32_t bh = b_addr + B1_BYTES + j * B2_BLOCK;
-            const uint64_t bhi = tc::smem_desc(bh, 128, 256), blo = tc::smem_desc(bh + B2_BLOCK / 2, 128, 256);
-            tc::mma_f16(tbase + face_col(i), ahi, bhi, id64, acc0);
-            tc::mma_f16(tbase + face_col(i), ahi, blo, id64, 1u);
-            tc::mma_f16(tbase + face_col(i), alo, bhi, id64, 1u);
+            const uint32_t bh = b_addr + j * BB_BLOCK;
+            const uint64_t bhi = tc::smem_desc(bh, 128, 256), blo = tc::smem_desc(bh + BB_BLOCK / 2, 128, 256);
+            tc::mma_f16(tbase + der_col(i), ahi, bhi, id96, acc0);
+            tc::mma_f16(tbase + der_col(i), ahi, blo, id96, 1u);
+            tc::mma_f16(tbase + der_col(i), alo, bhi, id96, 1u);
             if (j == c_kmap.last_of[q]) tc::commit(sten_done + i);
           }
           tc::commit(chunk_free + buf);
@@ -866,9 +868,9 @@ void recon33_fill_table(const double* w, float* out) {
 
 size_t recon33_tc_image_bytes() { return (size_t)r33::tcg::B_BYTES; }
 
-// FP16 hi/lo image of the weights in the tensor-core kernel's shared-memory layout: pass-1 blocks
-// (per k-step: 32 derivative columns of its stencil x 16 K, hi then lo), pass-2 blocks (64 face
-// columns x 16 K), then the power-of-two column scales (pass 1 per stencil, pass 2)
+// FP16 hi/lo image of the weights in the tensor-core kernel's shared-memory layout: per k-step one
+// block of 96 columns x 16 K (the 32 derivative columns of its stencil, then the 64 face columns),
+// hi then lo, then the power-of-two column scales (derivatives per stencil, faces)
 void recon33_tc_fill_image(const double* w, unsigned char* out) {
   using namespace r33;
   using namespace r33::tcg;
@@ -889,7 +891,7 @@ void recon33_tc_fill_image(const double* w, unsigned char* out) {
     if (pass == 1) return n < M ? w[woffq[q] + F * len + n * len + jin] : 0.0;
     return n < F ? w[woffq[q] + n * len + jin] : 0.0;
   };
-  float* cs = reinterpret_cast<float*>(out + B1_BYTES + B2_BYTES);
+  float* cs = reinterpret_cast<float*>(out + BB_BYTES);
   float scale1[NQ][32], scale2[64];
   for (int q = 0; q < NQ; ++q)
     for (int n = 0; n < 32; ++n) {
@@ -909,19 +911,18 @@ void recon33_tc_fill_image(const double* w, unsigned char* out) {
     scale2[n] = (float)std::ldexp(1.0, -e);
     cs[NQ * 32 + n] = (float)std::ldexp(1.0, e);
   }
-  auto put = [&](unsigned char* blk, int rows, int n, int k, float v) {
+  auto put = [&](unsigned char* blk, int n, int k, float v) {
     const __half hi = __float2half_rn(v);
     const __half lo = __float2half_rn(v - __half2float(hi));
     *reinterpret_cast<__half*>(blk + tile_byte(n, k)) = hi;
-    *reinterpret_cast<__half*>(blk + rows * 32 + tile_byte(n, k)) = lo;
+    *reinterpret_cast<__half*>(blk + BB_BLOCK / 2 + tile_byte(n, k)) = lo;
   };
   for (int j = 0; j < KS; ++j) {
     const int q = km.kq[j];
-    unsigned char* b1 = out + j * B1_BLOCK;
-    unsigned char* b2 = out + B1_BYTES + j * B2_BLOCK;
+    unsigned char* blk = out + j * BB_BLOCK;
     for (int k = 0; k < 16; ++k) {
-      for (int n = 0; n < 32; ++n) put(b1, 32, n, k, (float)(weight(1, n, 16 * j + k) * scale1[q][n]));
-      for (int n = 0; n < 64; ++n) put(b2, 64, n, k, (float)(weight(2, n, 16 * j + k) * scale2[n]));
+      for (int n = 0; n < 32; ++n) put(blk, n, k, (float)(weight(1, n, 16 * j + k) * scale1[q][n]));
+      for (int n = 0; n < 64; ++n) put(blk, 32 + n, k, (float)(weight(2, n, 16 * j + k) * scale2[n]));
     }
   }
 }
