@@ -548,12 +548,37 @@ static_assert(make_kmap().kq[KS - 1] == NQ - 1, "23 k-steps");
 static_assert(make_kmap().last_of[0] == 7, "S0 takes 8 k-steps");
 __constant__ KMap c_kmap = make_kmap();
 
+// per-k-step facts for the issuing thread and the consumers as compile-time bit patterns (no
+// constant-memory loads on the issue path): bit j of kFirst / kLast marks the first / last k-step
+// of a stencil, kLastPacked holds each stencil's last k-step in 5 bits
+constexpr uint32_t first_mask() {
+  uint32_t v = 0;
+  for (int j = 0; j < KS; ++j) v |= (uint32_t)make_kmap().first[j] << j;
+  return v;
+}
+constexpr uint32_t last_mask() {
+  uint32_t v = 0;
+  for (int q = 0; q < NQ; ++q) v |= 1u << make_kmap().last_of[q];
+  return v;
+}
+constexpr unsigned long long last_packed() {
+  unsigned long long v = 0;
+  for (int q = 0; q < NQ; ++q) v |= (unsigned long long)make_kmap().last_of[q] << (5 * q);
+  return v;
+}
+constexpr uint32_t kFirst = first_mask(), kLast = last_mask();
+constexpr unsigned long long kLastPacked = last_packed();
+static_assert(KS <= 31 && NQ * 5 <= 64, "bit patterns");
+__device__ __forceinline__ int last_kstep(int q) { return (int)((kLastPacked >> (5 * q)) & 31u); }
+__device__ __forceinline__ int kstep_stencil(int j) { return __popc(kFirst & ((2u << j) - 1u)) - 1; }
+
 // shared memory (bytes)
 struct TSmem {
   static constexpr int b_off = 0;
   static constexpr int a_off = B_BYTES;                          // ring of NB A buffers
   static constexpr int tile_off = a_off + NB * A_BUF;            // (NV + 1) x SN floats
-  static constexpr int pack_off = tile_off + (NV + 1) * SN * 4;  // gate parameters
+  static constexpr int koff_off = tile_off + (NV + 1) * SN * 4;  // tile offsets of the K columns
+  static constexpr int pack_off = koff_off + KT * 4;              // gate parameters
   static constexpr int bar_off = (pack_off + (int)sizeof(gate::Pack<3>) + 15) / 16 * 16;
   static constexpr int nbar = 2 * NB + 2 * NREG + 1;  // chunk_full, chunk_free, sten_done, reg_free, drain
   static constexpr int total = bar_off + 8 * nbar + 16;
@@ -590,6 +615,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
   uint64_t* reg_free = sten_done + NREG;  // every warp has read region i's occupant
   uint64_t* drain = reg_free + NREG;      // exit after a failed wait
   uint32_t* tbase_s = reinterpret_cast<uint32_t*>(drain + 1);
+  int* koff = reinterpret_cast<int*>(tsm + TSmem::koff_off);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r = tid & 127, h = tid >> 7;
@@ -599,6 +625,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
 
   // ---- once per CTA: B image, gate parameters, barriers, TMEM ----
   for (int i = tid; i < B_BYTES / 16; i += TCT) reinterpret_cast<uint4*>(Bs)[i] = __ldg(bimg + i);
+  for (int i = tid; i < KT; i += TCT) koff[i] = c_kmap.off[i];
   gate::Pack<3>* P = reinterpret_cast<gate::Pack<3>*>(tsm + TSmem::pack_off);
   if (mode == 2) gate::load_pack<3>(gpack, P);
   if (tid == 0) {
@@ -684,7 +711,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
     }
     const bool weno_row = active && (mode == 0 || (mode == 2 && !smooth) || (mode == 3 && !gate_mask[cell]));
     const bool weno_tile = __syncthreads_or(weno_row) != 0;
-    const int ks_end = weno_tile ? KS : c_kmap.last_of[0] + 1;
+    const int ks_end = weno_tile ? KS : last_kstep(0) + 1;
     const int nq_used = weno_tile ? NQ : 1;
 
 #pragma unroll 1
@@ -766,7 +793,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
             float xv[4], rs[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              const int o = c_kmap.off[16 * (j0 + jj) + 4 * h + e];
+              const int o = koff[16 * (j0 + jj) + 4 * h + e];
               xv[e] = (active && o != kPad) ? ref.delta(sm, c + o) * inv_s : 0.0f;
               rs[e] = xv[e] - __half2float(__float2half_rn(xv[e]));
             }
@@ -785,13 +812,14 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
         if (lane == 0) tc::mbar_arrive(chunk_full + buf);
         // stencils whose MMAs were issued in earlier chunks, before this chunk's MMAs (which may
         // need their regions)
-        while (nc < nq_used && c_kmap.last_of[nc] < j0) consume(nc++);
+        while (nc < nq_used && last_kstep(nc) < j0) consume(nc++);
         if (tid == 0) {
           if (!tc::mbar_wait(chunk_full + buf, use & 1u, WAIT_LIMIT)) ok = false;
           tc::fence_after_sync();
           for (int jj = 0; jj < nj; ++jj) {
-            const int j = j0 + jj, q = c_kmap.kq[j], i = q % NREG;
-            if (c_kmap.first[j]) {
+            const int j = j0 + jj, q = kstep_stencil(j), i = q % NREG;
+            const bool first = (kFirst >> j) & 1u;
+            if (first) {
               if ((rf_used >> i) & 1u) {
                 if (!tc::mbar_wait(reg_free + i, (rf_ph >> i) & 1u, WAIT_LIMIT)) ok = false;
                 rf_ph ^= 1u << i;
@@ -801,7 +829,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
             }
             // derivative and face columns of stencil q in one N = 96 MMA per product (all-linear
             // tiles compute the derivative columns too and ignore them)
-            const uint32_t acc0 = c_kmap.first[j] ? 0u : 1u;
+            const uint32_t acc0 = first ? 0u : 1u;
             const uint32_t ab = a_addr + buf * A_BUF + jj * A_KS;
             const uint64_t ahi = tc::smem_desc(ab, 128, 256), alo = tc::smem_desc(ab + A_KS / 2, 128, 256);
             const uint32_t bh = b_addr + j * BB_BLOCK;
@@ -809,7 +837,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
             tc::mma_f16(tbase + der_col(i), ahi, bhi, id96, acc0);
             tc::mma_f16(tbase + der_col(i), ahi, blo, id96, 1u);
             tc::mma_f16(tbase + der_col(i), alo, bhi, id96, 1u);
-            if (j == c_kmap.last_of[q]) tc::commit(sten_done + i);
+            if ((kLast >> j) & 1u) tc::commit(sten_done + i);
           }
           tc::commit(chunk_free + buf);
         }
