@@ -100,6 +100,21 @@ struct Ref {
     t = fmaf(-ut[2], sm[3 * SN + o] - uc[3], t);
     return gm1 * t;
   }
+  // delta(o) times a power of two inv_s, the scale folded into the row's last factor (1, 1 / rho~,
+  // gamma - 1): the same bits as delta(o) * inv_s
+  __device__ __forceinline__ float delta_scaled(const float* __restrict__ sm, int o, float fs) const {
+    const float dr = sm[o] - uc[0];
+    if (v == 0) return dr * fs;
+    if (v <= 3) return fmaf(-uv, dr, sm[v * SN + o] - uc[v]) * fs;
+    float t = fmaf(kin, dr, sm[4 * SN + o] - uc[4]);
+    t = fmaf(-ut[0], sm[SN + o] - uc[1], t);
+    t = fmaf(-ut[1], sm[2 * SN + o] - uc[2], t);
+    t = fmaf(-ut[2], sm[3 * SN + o] - uc[3], t);
+    return t * fs;
+  }
+  __device__ __forceinline__ float fold(float inv_s) const {
+    return v == 0 ? inv_s : (v <= 3 ? irt * inv_s : gm1 * inv_s);
+  }
 };
 
 // smoothness indicators beta_q (Eq. 22) of every stencil for one (cell, variable)
@@ -361,11 +376,20 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
                                                    const float* __restrict__ sp, int c, const double* __restrict__ U,
                                                    long long ncell, long long cell, long long fcell, long long ncell_f,
                                                    float* faces, bool active, int r, int h, float* xch, DW dwget) {
-  const int s_lo = 16 * h, s_hi = s_lo + 16 < F ? s_lo + 16 : F;
+  constexpr int P = 16, HP = 8;  // face points per quarter (the last quarter has F - 48 = 6), half
+  const int s_lo = P * h;
   const float gm1 = a.gammaf - 1.0f;
   float uc[NV], ut[3], kin, irt;
   float pt = 0.0f, rt = 1.0f, cq = 0.0f, th = 1.0f, thp = 1.0f;
   float p_min = 0.0f;
+  // dW of half a quarter (points s_lo + m0 ...), every load in flight at once
+  float dw[NV][HP];
+  auto load_half = [&](int m0) {
+#pragma unroll
+    for (int m = 0; m < HP; ++m)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dw[v][m] = (active && s_lo + m0 + m < F) ? dwget(s_lo + m0 + m, v) : 0.0f;
+  };
   if (active) {
     r32::cell_ref<3, 3>(sm, c, uc, ut, kin, irt);
     // central pressure: float32 where E/p < 8, else recovered in float64 from the state
@@ -397,8 +421,13 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
           }
       const float rho_max = rmax * a.hi_f, rho_min = rmin * a.lo_f;
       p_min = pmin * a.lo_f;
-      for (int s = s_lo; s < s_hi; ++s) {
-        const float rs = rt + dwget(s, 0);
+      float d0[P];
+#pragma unroll
+      for (int m = 0; m < P; ++m) d0[m] = s_lo + m < F ? dwget(s_lo + m, 0) : 0.0f;
+#pragma unroll
+      for (int m = 0; m < P; ++m) {
+        if (s_lo + m >= F) continue;
+        const float rs = rt + d0[m];
         if (rs < rho_min) th = fminf(th, (rt - rho_min) / (rt - rs));
         if (rs > rho_max) th = fminf(th, (rho_max - rt) / (rs - rt));
       }
@@ -414,23 +443,28 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
       return rr > 0.0f && (fmaf(t, dp, pt) - p_min) * rr >= cq * t * t * du2;
     };
 #pragma unroll 1
-    for (int s = s_lo; s < s_hi; ++s) {
-      const float dr = th * dwget(s, 0);
-      const float dp = th * dwget(s, NV - 1);
-      float du2 = 0.0f;
+    for (int m0 = 0; m0 < P; m0 += HP) {
+      load_half(m0);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float du = th * dwget(s, 1 + k);
-        du2 = fmaf(du, du, du2);
-      }
-      if (admissible(1.0f, dr, dp, du2)) continue;
-      float lo = 0.0f, hi = 1.0f;
+      for (int m = 0; m < HP; ++m) {
+        if (s_lo + m0 + m >= F) continue;
+        const float dr = th * dw[0][m];
+        const float dp = th * dw[NV - 1][m];
+        float du2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float du = th * dw[1 + k][m];
+          du2 = fmaf(du, du, du2);
+        }
+        if (admissible(1.0f, dr, dp, du2)) continue;
+        float lo = 0.0f, hi = 1.0f;
 #pragma unroll 1
-      for (int it = 0; it < 40; ++it) {
-        const float mid = 0.5f * (lo + hi);
-        if (admissible(mid, dr, dp, du2)) lo = mid; else hi = mid;
+        for (int it = 0; it < 40; ++it) {
+          const float mid = 0.5f * (lo + hi);
+          if (admissible(mid, dr, dp, du2)) lo = mid; else hi = mid;
+        }
+        thp = fminf(thp, lo);
       }
-      thp = fminf(thp, lo);
     }
   }
   xch[512 + h * 128 + r] = thp;
@@ -440,22 +474,28 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
   const float scl = th * thp;
   float4* out4 = reinterpret_cast<float4*>(faces);
 #pragma unroll 1
-  for (int s = s_lo; s < s_hi; ++s) {
-    const float dr = scl * dwget(s, 0);
-    const float rs = rt + dr;
-    const float irs = __frcp_rn(rs);
-    float du2 = 0.0f, uo[3];
+  for (int m0 = 0; m0 < P; m0 += HP) {
+    load_half(m0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float du = scl * dwget(s, 1 + k);
-      du2 = fmaf(du, du, du2);
-      uo[k] = fmaf(rt * du, irs, ut[k]);
+    for (int m = 0; m < HP; ++m) {
+      const int s = s_lo + m0 + m;
+      if (s >= F) continue;
+      const float dr = scl * dw[0][m];
+      const float rs = rt + dr;
+      const float irs = __frcp_rn(rs);
+      float du2 = 0.0f, uo[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float du = scl * dw[1 + k][m];
+        du2 = fmaf(du, du, du2);
+        uo[k] = fmaf(rt * du, irs, ut[k]);
+      }
+      const float dp = scl * dw[NV - 1][m];
+      const float ps = fmaf(-cq * du2, irs, pt + dp);
+      // float32 layout: [s][cell] float4 (rho, u, v, p), then the plane [s][cell] of w
+      out4[(long long)s * ncell_f + fcell] = make_float4(rs, uo[0], uo[1], ps);
+      faces[4LL * F * ncell_f + (long long)s * ncell_f + fcell] = uo[2];
     }
-    const float dp = scl * dwget(s, NV - 1);
-    const float ps = fmaf(-cq * du2, irs, pt + dp);
-    // float32 layout: [s][cell] float4 (rho, u, v, p), then the plane [s][cell] of w
-    out4[(long long)s * ncell_f + fcell] = make_float4(rs, uo[0], uo[1], ps);
-    faces[4LL * F * ncell_f + (long long)s * ncell_f + fcell] = uo[2];
   }
 }
 
@@ -715,7 +755,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
     const int nq_used = weno_tile ? NQ : 1;
 
 #pragma unroll 1
-    for (int v = 0; v < NV && ok; ++v) {
+    for (int v = 0; v < NV; ++v) {
       const Ref ref(sm, c, v, gm1);
       // s = power of two at or above the central cell's scale of this variable
       const float pc = sp[c];
@@ -723,6 +763,7 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
       int ex = 0;
       if (scale > 0.0f && scale < 3.0e38f) frexpf(scale, &ex);
       const float inv_s = ldexpf(1.0f, -ex), sc = ldexpf(1.0f, ex);
+      const float fs = ref.fold(inv_s);
       const float eps_s = fminf(ldexpf(a.epsf, -4 * ex), 1.0e30f);  // eps / s^4
 
       float acc[16];
@@ -790,18 +831,20 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
 #pragma unroll
         for (int jj = 0; jj < KPC; ++jj) {
           if (jj < nj) {
-            float xv[4], rs[4];
+            float xv[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int o = koff[16 * (j0 + jj) + 4 * h + e];
-              xv[e] = (active && o != kPad) ? ref.delta(sm, c + o) * inv_s : 0.0f;
-              rs[e] = xv[e] - __half2float(__float2half_rn(xv[e]));
+              xv[e] = (active && o != kPad) ? ref.delta_scaled(sm, c + o, fs) : 0.0f;
             }
+            // hi = FP16 rounding of each value (one rounding per pair), lo = FP16 of the remainder
+            const __half2 h01 = __floats2half2_rn(xv[0], xv[1]), h23 = __floats2half2_rn(xv[2], xv[3]);
+            const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
             uint2 hi, lo;
-            hi.x = pack_half2(xv[0], xv[1]);
-            hi.y = pack_half2(xv[2], xv[3]);
-            lo.x = pack_half2(rs[0], rs[1]);
-            lo.y = pack_half2(rs[2], rs[3]);
+            hi.x = *reinterpret_cast<const uint32_t*>(&h01);
+            hi.y = *reinterpret_cast<const uint32_t*>(&h23);
+            lo.x = pack_half2(xv[0] - f01.x, xv[1] - f01.y);
+            lo.y = pack_half2(xv[2] - f23.x, xv[3] - f23.y);
             *reinterpret_cast<uint2*>(base + jj * A_KS + ob) = hi;
             *reinterpret_cast<uint2*>(base + jj * A_KS + A_KS / 2 + ob) = lo;
           }
@@ -853,8 +896,10 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
           if (sp_ < F) *slot(faces, ncell_f, fcell, sp_, v) = acc[m] * inv_w * cs2[sp_] * sc;
         }
       }
-      ok = __syncthreads_and(ok) != 0;
     }
+    // one CTA-wide check per tile (nothing between the variables needs a CTA barrier: the ring,
+    // the TMEM regions and the dW slots each have their own hand-offs)
+    ok = __syncthreads_and(ok) != 0;
     if (!ok) break;
     // the tail, four threads per cell: each reads back only the dW slots it wrote itself; the A ring
     // (every MMA consumed) holds the limiter's exchange
