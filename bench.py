@@ -111,7 +111,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--path", choices=["auto", "fp64", "fp64char", "fp32", "gated", "kxrcf"], default="auto")
+    ap.add_argument("--path", choices=["auto", "fp64", "fp64char", "fp32", "fp32char", "gated", "kxrcf"],
+                    default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline path only (no other paths, e2e or CPU baseline): for profiler runs")
@@ -326,11 +327,11 @@ def make_solver(W, path, n=None, bc=None):
 
     from paper_2401_16543_gb300 import KFVM
     g = KFVM(list(n or W.n), dims=W.dims, radius=W.R, bc=bc or W.bc)
-    if path in ("fp32", "gated", "kxrcf"):
+    if path in ("fp32", "fp32char", "gated", "kxrcf"):
         g.set_option("precision", 32)
     if path == "kxrcf":  # the paper's troubled-cell indicator (Sec. 3.5) instead of the learned gate
         g.set_option("recon", 4)
-    if path == "fp64char":  # plain FP64 WENO-AO in characteristic variables (Sec. 3.4.1)
+    if path in ("fp64char", "fp32char"):  # WENO-AO in characteristic variables (Sec. 3.4.1)
         g.set_option("variables", 1)
     if path == "gated":
         g.gate_set_params(np.load(W.gate_path()))
@@ -483,9 +484,11 @@ def main():
 
     # ---- the other paths on the same workload (plain FP64 is the metric's reference) ----
     others = {}
-    for other in ("fp64", "fp64char", "fp32", "gated", "kxrcf"):
+    for other in ("fp64", "fp64char", "fp32", "fp32char", "gated", "kxrcf"):
         if args.headline_only or other == path or (other == "gated" and not W.has_gate()):
             continue
+        if other == "fp32char" and W.dims == 3 and W.R == 3:
+            continue  # the radius-3 3D kernels reconstruct in linearized primitive variables only
         if other == "fp64char" and W.fp64_planes:
             continue  # radius 3 in float64 on 512^2 x 16 cells: ~25 s per step with three sets of weights
         k = max(3, args.steps // 4)
@@ -589,7 +592,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp64char": "f64", "fp32": "f32", "gated": "f32+bf16", "kxrcf": "f32"}[path],
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp64char": "f64", "fp32": "f32", "fp32char": "f32", "gated": "f32+bf16",
+                      "kxrcf": "f32"}[path],
             "data": "synthetic",
             "config": {"workload": W.desc, "name": W.name, "grid": W.n, "radius": W.R, "path": path,
                        "gate": ({"params": f"paper_2401_16543_gb300/{W.gate}",

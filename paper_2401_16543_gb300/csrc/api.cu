@@ -186,7 +186,8 @@ kfvm_status check_ready(kfvm_ctx* ctx) {
   if (!ctx) return KFVM_ERR_ARG;
   if (!ctx->weights_built) return KFVM_ERR_STATE;
   if (ctx->recon == 2 && !ctx->gate_loaded) return KFVM_ERR_STATE;
-  if (ctx->vars == 1 && ctx->precision == 32) return KFVM_ERR_STATE;  // characteristic: FP64 kernels only
+  // characteristic variables in float32: d = 2 and d = 3 radius 2 (the radius-3 3D kernels are lin-prim only)
+  if (ctx->vars == 1 && ctx->precision == 32 && ctx->dims == 3 && ctx->R == 3) return KFVM_ERR_STATE;
   return KFVM_OK;
 }
 

@@ -327,7 +327,111 @@ __device__ __forceinline__ void write_states(const GridArgs& a, const float* __r
   }
 }
 
-template <int D, int R>
+// Characteristic variables of direction dir (Sec. 3.4.1) in float32 at the central average uc, from
+// its velocity ut, kinetic energy per mass kin and 1/rho irt: L (rows: left eigenvectors of the flux
+// Jacobian of dir) and Rm (columns: right eigenvectors).  Waves u_n - c, entropy, the shear waves of
+// the tangential axes in increasing order, u_n + c; b1 = (gamma-1)/c^2, b2 = b1 |u|^2/2,
+// H = (E+p)/rho.
+template <int D>
+__device__ __forceinline__ void char_matrices32(const float* uc, const float* ut, float kin, float irt, float pc,
+                                                float gamma, int dir, float (&L)[D + 2][D + 2],
+                                                float (&Rm)[D + 2][D + 2]) {
+  constexpr int NV = D + 2;
+  const float c = sqrtf(gamma * pc * irt), ic = __frcp_rn(c), H = (uc[NV - 1] + pc) * irt;
+  const float q2 = 2.0f * kin;
+  const float b1 = (gamma - 1.0f) * ic * ic, b2 = 0.5f * b1 * q2, un = ut[dir];
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) L[i][j] = Rm[i][j] = 0.0f;
+  Rm[0][0] = Rm[0][1] = Rm[0][NV - 1] = 1.0f;
+  L[0][0] = 0.5f * (b2 + un * ic);
+  L[1][0] = 1.0f - b2;
+  L[NV - 1][0] = 0.5f * (b2 - un * ic);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float nk = (k == dir) ? 1.0f : 0.0f;
+    Rm[1 + k][0] = ut[k] - c * nk;
+    Rm[1 + k][1] = ut[k];
+    Rm[1 + k][NV - 1] = ut[k] + c * nk;
+    L[0][1 + k] = 0.5f * (-b1 * ut[k] - nk * ic);
+    L[1][1 + k] = b1 * ut[k];
+    L[NV - 1][1 + k] = 0.5f * (-b1 * ut[k] + nk * ic);
+  }
+  Rm[NV - 1][0] = H - c * un;
+  Rm[NV - 1][1] = 0.5f * q2;
+  Rm[NV - 1][NV - 1] = H + c * un;
+  L[0][NV - 1] = 0.5f * b1;
+  L[1][NV - 1] = -b1;
+  L[NV - 1][NV - 1] = 0.5f * b1;
+  int w = 2;
+#pragma unroll
+  for (int t = 0; t < D; ++t) {
+    if (t == dir) continue;
+    Rm[1 + t][w] = 1.0f;
+    Rm[NV - 1][w] = ut[t];
+    L[w][0] = -ut[t];
+    L[w][1 + t] = 1.0f;
+    ++w;
+  }
+}
+
+// row Lv of L applied to U_l - U_c for every S0 cell l (characteristic deltas relative to the centre)
+template <int D, int R, int... Ls>
+__device__ __forceinline__ void gather_char(const float* __restrict__ sm, int c, const float* Lv, const float* uc,
+                                            float (&g)[Geo<D, R>::N0], std::integer_sequence<int, Ls...>) {
+  constexpr int SN = T32<D, R>::SN, NV = D + 2;
+  auto one = [&](int o) {
+    float t = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) t = fmaf(Lv[j], sm[j * SN + o] - uc[j], t);
+    return t;
+  };
+  ((g[Ls] = one(c + Dlt<D, R, Ls>::v)), ...);
+}
+
+// WENO-AO values (Eq. 19) at the face points S0 + k, k < 2 NT: the two faces normal to one direction
+template <int D, int R, int S0, int... Ks>
+__device__ __forceinline__ void faces_weno_range(const W32<D, R>& W, const float (&g)[Geo<D, R>::N0],
+                                                 const float (&coef)[Geo<D, R>::NQ], float* out, int stride,
+                                                 std::integer_sequence<int, Ks...>) {
+  ((out[(S0 + Ks) * stride] = face_blend<D, R, S0 + Ks>(W, g, coef, std::make_integer_sequence<int, Geo<D, R>::NQ>{})),
+   ...);
+}
+
+// nonlinear weights in the scaled form (reading of Eq. 24 for float32) and the WENO-AO coefficients
+// of Eq. 19 from the smoothness indicators of one (cell, variable)
+template <int D, int NQ>
+__device__ __forceinline__ void weno_coefficients(const float (&beta)[NQ], float epsf, float (&coef)[NQ]) {
+  float bmax = 0.0f;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) bmax = fmaxf(bmax, beta[q]);
+  if (bmax > 0.0f) {
+    const float ib = __frcp_rn(bmax);
+    const float e = fmaxf(epsf * ib * ib, 1e-30f);
+    float om[NQ], sum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const float bq = beta[q] * ib;
+      om[q] = __fdividef((float)linear_weight<D>(q), fmaf(bq, bq, e));
+      sum += om[q];
+    }
+    const float inv = __frcp_rn(sum);
+    const float w0 = om[0] * inv;
+    coef[0] = w0 / (float)linear_weight<D>(0);
+#pragma unroll
+    for (int q = 1; q < NQ; ++q) coef[q] = fmaf(-w0, (float)(linear_weight<D>(q) / linear_weight<D>(0)), om[q] * inv);
+  } else {
+    coef[0] = 1.0f;
+#pragma unroll
+    for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
+  }
+}
+
+// CH: WENO-AO cells in characteristic variables (Sec. 3.4.1), a separate instantiation; the values
+// at a direction's face points are reconstructed in that direction's characteristic deltas with their
+// own weights, then taken back (R, then Phi) to the linearized primitive deltas the tail expects.
+template <int D, int R, bool CH = false>
 __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1) recon32_kernel(GridArgs a, int mode,
                                                                      const double* __restrict__ U,
                                                                      const float* __restrict__ S,
@@ -445,36 +549,34 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
     const int oc = (olx + T::H) + T::SX * ((oly + T::H) + T::SY * (D == 3 ? olz + T::H : 0));
     float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
     cell_ref<D, R>(sm, oc, uc, ut, kin, irt);
-    float g[N0];
-    gather_row<D, R>(sm, oc, v, g, uc, ut, kin, irt, gm1, SEQ_L);
-    float beta[NQ];
-    all_betas<D, R>(W, g, beta, std::make_integer_sequence<int, NQ>{});
-    float bmax = 0.0f;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) bmax = fmaxf(bmax, beta[q]);
-    float coef[NQ];
-    if (bmax > 0.0f) {
-      const float ib = __frcp_rn(bmax);
-      const float e = fmaxf(a.epsf * ib * ib, 1e-30f);
-      float om[NQ], sum = 0.0f;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const float bq = beta[q] * ib;
-        om[q] = __fdividef((float)linear_weight<D>(q), fmaf(bq, bq, e));
-        sum += om[q];
-      }
-      const float inv = __frcp_rn(sum);
-      const float w0 = om[0] * inv;
-      coef[0] = w0 / (float)linear_weight<D>(0);
-#pragma unroll
-      for (int q = 1; q < NQ; ++q)
-        coef[q] = fmaf(-w0, (float)(linear_weight<D>(q) / linear_weight<D>(0)), om[q] * inv);
+    float g[N0], beta[NQ], coef[NQ];
+    if constexpr (!CH) {
+      gather_row<D, R>(sm, oc, v, g, uc, ut, kin, irt, gm1, SEQ_L);
+      all_betas<D, R>(W, g, beta, std::make_integer_sequence<int, NQ>{});
+      weno_coefficients<D, NQ>(beta, a.epsf, coef);
+      all_faces_weno<D, R>(W, g, coef, dw + owner + v * TH, NV * TH, SEQ_S);
     } else {
-      coef[0] = 1.0f;
+      // component v of each direction's characteristic variables, weights per direction, values at
+      // that direction's two faces (slots of the characteristic component v until the back transform)
+      constexpr int NT = G::NT;
+      constexpr auto SEQ_F = std::make_integer_sequence<int, 2 * NT>{};
 #pragma unroll
-      for (int q = 1; q < NQ; ++q) coef[q] = 0.0f;
+      for (int dir = 0; dir < D; ++dir) {
+        float L[NV][NV], Rm[NV][NV];
+        char_matrices32<D>(uc, ut, kin, irt, sp[oc], a.gammaf, dir, L, Rm);
+        float Lv[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) Lv[j] = L[v][j];
+        gather_char<D, R>(sm, oc, Lv, uc, g, SEQ_L);
+        all_betas<D, R>(W, g, beta, std::make_integer_sequence<int, NQ>{});
+        weno_coefficients<D, NQ>(beta, a.epsf, coef);
+        float* out = dw + owner + v * TH;
+        if (dir == 0) faces_weno_range<D, R, 0>(W, g, coef, out, NV * TH, SEQ_F);
+        if (dir == 1) faces_weno_range<D, R, 2 * NT>(W, g, coef, out, NV * TH, SEQ_F);
+        if constexpr (D == 3)
+          if (dir == 2) faces_weno_range<D, R, 4 * NT>(W, g, coef, out, NV * TH, SEQ_F);
+      }
     }
-    all_faces_weno<D, R>(W, g, coef, dw + owner + v * TH, NV * TH, SEQ_S);
   };
   if (mode == 0) {
     // every active cell is a WENO cell: each thread its own cell, variable by variable
@@ -490,6 +592,42 @@ __global__ void __launch_bounds__(T32<D, R>::THREADS, (D == 2 && R == 2) ? 3 : 1
   }
   __syncthreads();
   if (!active) return;
+  if constexpr (CH) {
+    // characteristic values of this WENO-AO cell back to conservative deltas (R) and to the
+    // linearized primitive deltas of the tail (Phi): dW = Phi R w at every face point
+    if (weno_here) {
+      constexpr int NT = G::NT;
+      float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin, irt;
+      cell_ref<D, R>(sm, c, uc, ut, kin, irt);
+#pragma unroll 1
+      for (int dir = 0; dir < D; ++dir) {
+        float L[NV][NV], Rm[NV][NV];
+        char_matrices32<D>(uc, ut, kin, irt, sp[c], a.gammaf, dir, L, Rm);
+#pragma unroll 1
+        for (int k = 0; k < 2 * NT; ++k) {
+          const int s = 2 * dir * NT + k;
+          float w[NV], du[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) w[v] = mydw[(s * NV + v) * TH];
+#pragma unroll
+          for (int i = 0; i < NV; ++i) {
+            float t = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) t = fmaf(Rm[i][j], w[j], t);
+            du[i] = t;
+          }
+          mydw[(s * NV + 0) * TH] = du[0];
+          float pi = fmaf(kin, du[0], du[NV - 1]);
+#pragma unroll
+          for (int k2 = 0; k2 < D; ++k2) {
+            mydw[(s * NV + 1 + k2) * TH] = fmaf(-ut[k2], du[0], du[1 + k2]) * irt;
+            pi = fmaf(-ut[k2], du[1 + k2], pi);
+          }
+          mydw[(s * NV + NV - 1) * TH] = gm1 * pi;
+        }
+      }
+    }
+  }
 
   // ---- tail: central pressure in float64, limiter, primitive Riemann states ----
   write_states<D, R>(a, sm, sp, c, U, ncell, cell, fcell, ncell_f, faces,
@@ -661,7 +799,7 @@ cudaError_t launch(kfvm_ctx* ctx, const double* U, const float* shadow, float* f
                     ((D == 3) ? (a.zf_count + T::TZ - 1) / T::TZ : 1);
   const bool learned = ctx->recon == 2;
   const size_t smem = sizeof(float) * (learned ? Smem32<D, R>::total_gate : Smem32<D, R>::base);
-  auto kern = recon32_kernel<D, R>;
+  auto kern = ctx->vars == 1 ? recon32_kernel<D, R, true> : recon32_kernel<D, R, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(float) * Smem32<D, R>::total_gate));
   if (e != cudaSuccess) return e;
