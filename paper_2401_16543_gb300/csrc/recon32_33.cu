@@ -367,29 +367,26 @@ __global__ void __launch_bounds__(TH) label33_kernel(GridArgs a, const double* _
 
 // Tail of one cell shared by its four threads of the tensor-core kernel (quarter h owns the face
 // points 16 h ... 16 h + 15): the same arithmetic as r32::write_states -- central pressure (float64
-// where E/p shows cancellation), positivity limiter (Sec. 4) on the reconstructed dW = dwget(s, v),
-// float32 primitive Riemann states -- with the limiter's theta_rho and theta_p, minima over all 54
-// points, combined through shared memory (xch: 2 x 4 x 128 floats).  Every thread of the CTA calls
-// it (it holds two CTA barriers); inactive rows only take part in the barriers.
-template <class DW>
+// where E/p shows cancellation), positivity limiter (Sec. 4) on the reconstructed dW, float32
+// primitive Riemann states -- with the limiter's theta_rho and theta_p, minima over all 54 points,
+// combined through shared memory (xch: 2 x 4 x 128 floats).  The quarter's dW come from two loaders
+// that every thread calls (they may read tensor memory, which takes the whole warp): ld_rho(d) the
+// density deltas of its 16 points, ld_half(m0, dw) all variables of points m0 ... m0 + 7.  Every
+// thread of the CTA calls it (it holds two CTA barriers); inactive rows only take part.
+template <class LdRho, class LdHalf>
 __device__ __forceinline__ void write_states_split(const GridArgs& a, const float* __restrict__ sm,
                                                    const float* __restrict__ sp, int c, const double* __restrict__ U,
                                                    long long ncell, long long cell, long long fcell, long long ncell_f,
-                                                   float* faces, bool active, int r, int h, float* xch, DW dwget) {
+                                                   float* faces, bool active, int r, int h, float* xch, LdRho ld_rho,
+                                                   LdHalf ld_half) {
   constexpr int P = 16, HP = 8;  // face points per quarter (the last quarter has F - 48 = 6), half
   const int s_lo = P * h;
   const float gm1 = a.gammaf - 1.0f;
-  float uc[NV], ut[3], kin, irt;
+  float uc[NV], ut[3] = {0.f, 0.f, 0.f}, kin = 0.0f, irt = 1.0f;
   float pt = 0.0f, rt = 1.0f, cq = 0.0f, th = 1.0f, thp = 1.0f;
   float p_min = 0.0f;
-  // dW of half a quarter (points s_lo + m0 ...), every load in flight at once
-  float dw[NV][HP];
-  auto load_half = [&](int m0) {
-#pragma unroll
-    for (int m = 0; m < HP; ++m)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) dw[v][m] = (active && s_lo + m0 + m < F) ? dwget(s_lo + m0 + m, v) : 0.0f;
-  };
+  float d0[P];
+  ld_rho(d0);
   if (active) {
     r32::cell_ref<3, 3>(sm, c, uc, ut, kin, irt);
     // central pressure: float32 where E/p < 8, else recovered in float64 from the state
@@ -421,9 +418,6 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
           }
       const float rho_max = rmax * a.hi_f, rho_min = rmin * a.lo_f;
       p_min = pmin * a.lo_f;
-      float d0[P];
-#pragma unroll
-      for (int m = 0; m < P; ++m) d0[m] = s_lo + m < F ? dwget(s_lo + m, 0) : 0.0f;
 #pragma unroll
       for (int m = 0; m < P; ++m) {
         if (s_lo + m >= F) continue;
@@ -436,15 +430,17 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
   xch[h * 128 + r] = th;
   __syncthreads();
   th = fminf(fminf(xch[r], xch[128 + r]), fminf(xch[256 + r], xch[384 + r]));
-  if (active && a.positivity) {
+  float dw[NV][HP];
+  if (a.positivity) {
     // p(theta) >= p_min  <=>  (pt + theta dpi - p_min) (rt + theta drho) >= cq theta^2 |du|^2
     auto admissible = [&](float t, float dr, float dp, float du2) {
       const float rr = fmaf(t, dr, rt);
       return rr > 0.0f && (fmaf(t, dp, pt) - p_min) * rr >= cq * t * t * du2;
     };
-#pragma unroll 1
+#pragma unroll
     for (int m0 = 0; m0 < P; m0 += HP) {
-      load_half(m0);
+      ld_half(m0, dw);
+      if (!active) continue;
 #pragma unroll
       for (int m = 0; m < HP; ++m) {
         if (s_lo + m0 + m >= F) continue;
@@ -470,12 +466,12 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
   xch[512 + h * 128 + r] = thp;
   __syncthreads();
   thp = fminf(fminf(xch[512 + r], xch[640 + r]), fminf(xch[768 + r], xch[896 + r]));
-  if (!active) return;
   const float scl = th * thp;
   float4* out4 = reinterpret_cast<float4*>(faces);
-#pragma unroll 1
+#pragma unroll
   for (int m0 = 0; m0 < P; m0 += HP) {
-    load_half(m0);
+    ld_half(m0, dw);
+    if (!active) continue;
 #pragma unroll
     for (int m = 0; m < HP; ++m) {
       const int s = s_lo + m0 + m;
@@ -539,7 +535,7 @@ constexpr int KT = KS * 16;                // padded K = 368
 constexpr int TCT = 512;                   // threads per CTA: 4 per cell row (a quarter of each k-step)
 constexpr int KPC = 2;                     // MMA k-steps per ring chunk (one CTA barrier per chunk)
 constexpr int NB = 2;                      // A ring buffers
-constexpr int NREG = 4;                    // TMEM regions, one stencil's accumulators each
+constexpr int NREG = 2;                    // TMEM regions, one stencil's accumulators each
 constexpr int NOUT = 96;                   // MMA columns per k-step: 32 derivative + 64 face values
 constexpr int BB_BLOCK = NOUT * 16 * 2 * 2;  // B block of one k-step: 96 x 16 FP16, hi + lo
 constexpr int BB_BYTES = KS * BB_BLOCK;
@@ -552,7 +548,13 @@ constexpr int WAIT_LIMIT = 1 << 22;
 // TMEM columns of region i (128 apart): the 32 derivative columns, then the 64 face columns
 __host__ __device__ constexpr uint32_t der_col(int i) { return 128u * (uint32_t)i; }
 __host__ __device__ constexpr uint32_t face_col(int i) { return 128u * (uint32_t)i + 32u; }
-static_assert(der_col(NREG - 1) + NOUT <= 512, "four regions of 96 TMEM columns");
+// where quarter h parks the blended dW of variable v until the tail: columns 256 + 64 v + 16 h for
+// v < 4; the last variable in the 32 columns each region leaves free (96 ... 127, 224 ... 255)
+__host__ __device__ constexpr uint32_t park_col(int v, int h) {
+  return v < NV - 1 ? 256u + 64u * (uint32_t)v + 16u * (uint32_t)h
+                    : 96u + 128u * (uint32_t)(h >> 1) + 16u * (uint32_t)(h & 1);
+}
+static_assert(NREG == 2 && der_col(1) + NOUT <= 224 && park_col(NV - 2, 3) + 16 <= 512, "TMEM columns");
 
 struct KMap {
   int kq[KS];       // stencil of each k-step
@@ -887,25 +889,32 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
         ++it;
       }
       while (nc < nq_used) consume(nc++);
-      // blended face values / sum_q w~_q, back in the variable's units
+      // blended face values / sum_q w~_q, back in the variable's units, parked in tensor memory (the
+      // last variable in registers) until the tail
       const float inv_w = weno_row ? __frcp_rn(wsum) : 1.0f;
-      if (active) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const int sp_ = 16 * h + m;
-          if (sp_ < F) *slot(faces, ncell_f, fcell, sp_, v) = acc[m] * inv_w * cs2[sp_] * sc;
-        }
-      }
+      for (int m = 0; m < 16; ++m) acc[m] = 16 * h + m < F ? acc[m] * inv_w * cs2[16 * h + m] * sc : 0.0f;
+      tc::tmem_st16(tbase + lane_base + park_col(v, h), acc);
     }
     // one CTA-wide check per tile (nothing between the variables needs a CTA barrier: the ring,
     // the TMEM regions and the dW slots each have their own hand-offs)
     ok = __syncthreads_and(ok) != 0;
     if (!ok) break;
-    // the tail, four threads per cell: each reads back only the dW slots it wrote itself; the A ring
-    // (every MMA consumed) holds the limiter's exchange
+    // the tail, four threads per cell, on the dW each thread parked itself in tensor memory; the A
+    // ring (every MMA consumed) holds the limiter's exchange
+    tc::fence_after_sync();
+    auto ld_rho = [&](float (&d)[16]) { tc::tmem_ld16(tbase + lane_base + park_col(0, h), d); };
+    auto ld_half = [&](int m0, float (&d)[NV][8]) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        float t8[8];
+        tc::tmem_ld8(tbase + lane_base + park_col(v, h) + (uint32_t)m0, t8);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) d[v][m] = t8[m];
+      }
+    };
     write_states_split(a, sm, sp, c, U, (long long)a.n[0] * a.n[1] * a.n[2], cell, fcell, ncell_f, faces, active, r,
-                       h, reinterpret_cast<float*>(As),
-                       [&](int s_, int v_) { return *slot(faces, ncell_f, fcell, s_, v_); });
+                       h, reinterpret_cast<float*>(As), ld_rho, ld_half);
   }
   if (!ok) {
     if (tid == 0) raise_flag(a.status, kFlagTimeout);
