@@ -534,6 +534,8 @@ def main():
     e2e = {"value": job_value(world, ncell, args.steps, ms_e2e), "unit": "cell-updates/s",
            "h2d_bytes_per_step": U0.numel() * 8, "d2h_bytes_per_step": U0.numel() * 8,
            "pipelining": "double-buffered: upload k+1 and download k-1 overlap step k",
+           "input": "every step uploads the workload's initial state (value advances the state through its steps; "
+                    "the gate's share of linear cells changes as the state evolves)",
            "l2": "flushed before every step, inside the timed region"}
 
     # ---- roofline of the dominant kernel ----
