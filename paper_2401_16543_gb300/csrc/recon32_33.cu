@@ -84,16 +84,17 @@ __device__ __forceinline__ float* slot(float* faces, long long ncell_f, long lon
 // reference state of a tile cell and the lin-prim delta of one variable (Eq. 33, relative to
 // the centre: row v of Phi applied to U_o - U_c)
 struct Ref {
-  float uc[NV], ut[3], kin, irt, uv, gm1;
+  float uc[NV], ut[3], kin, irt, uv, ucv, gm1;  // ucv = uc[v], kept out of the runtime-indexed array
   int v;
   __device__ __forceinline__ Ref(const float* __restrict__ sm, int cc, int var, float gm1_) : gm1(gm1_), v(var) {
     r32::cell_ref<3, 3>(sm, cc, uc, ut, kin, irt);
     uv = v == 1 ? ut[0] : (v == 2 ? ut[1] : ut[2]);
+    ucv = v == 1 ? uc[1] : (v == 2 ? uc[2] : uc[3]);
   }
   __device__ __forceinline__ float delta(const float* __restrict__ sm, int o) const {
     const float dr = sm[o] - uc[0];
     if (v == 0) return dr;
-    if (v <= 3) return fmaf(-uv, dr, sm[v * SN + o] - uc[v]) * irt;
+    if (v <= 3) return fmaf(-uv, dr, sm[v * SN + o] - ucv) * irt;
     float t = fmaf(kin, dr, sm[4 * SN + o] - uc[4]);
     t = fmaf(-ut[0], sm[SN + o] - uc[1], t);
     t = fmaf(-ut[1], sm[2 * SN + o] - uc[2], t);
@@ -105,7 +106,7 @@ struct Ref {
   __device__ __forceinline__ float delta_scaled(const float* __restrict__ sm, int o, float fs) const {
     const float dr = sm[o] - uc[0];
     if (v == 0) return dr * fs;
-    if (v <= 3) return fmaf(-uv, dr, sm[v * SN + o] - uc[v]) * fs;
+    if (v <= 3) return fmaf(-uv, dr, sm[v * SN + o] - ucv) * fs;
     float t = fmaf(kin, dr, sm[4 * SN + o] - uc[4]);
     t = fmaf(-ut[0], sm[SN + o] - uc[1], t);
     t = fmaf(-ut[1], sm[2 * SN + o] - uc[2], t);

@@ -4,7 +4,7 @@
 
 Launches, in order: the FP64 path (build_weights, max_rate, recon64, flux_update), the flux-only
 entry (face_flux, update) and recon64 in characteristic variables on 2D 256^2; the FP32 path in 3D radius 2 (shadow, recon32<3,2>,
-flux_update) on 48^3; 3D radius 3 on 32^3 (recon33 on the FP32 pipe, recon33_tc on the tensor
+flux_update, and recon32<3,2> in characteristic variables) on 48^3; 3D radius 3 on 32^3 (recon33 on the FP32 pipe, recon33_tc on the tensor
 cores, label33); the learned gate (features, label, forward, mask, train, adam) and the KXRCF
 indicator (float64 and float32) on the 2D grid.
 Every computation goes through the C ABI; results are not checked here (the tests do that).
@@ -56,6 +56,9 @@ def main() -> None:
     h = KFVM([48, 48, 48], dims=3, radius=2, bc="periodic")
     h.set_option("precision", 32)
     h.step(U3.clone(), 0.4)
+    h.set_option("variables", 1)
+    h.reconstruct(U3)
+    h.set_option("variables", 0)
     # 3D radius 3: FP32 pipe, tensor cores, labels
     V = workloads.mixed_voronoi(3, 32, 4, seed=5, R=3, device=dev).contiguous()
     t = KFVM([32, 32, 32], dims=3, radius=3, bc="outflow")
