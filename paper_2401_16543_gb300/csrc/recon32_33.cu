@@ -783,11 +783,12 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
         sd_ph ^= 1u << i;
         tc::fence_after_sync();
         float cq = q == 0 ? 1.0f : 0.0f;  // linear rows: S0 alone
+        float f[16];
         if (weno_tile) {
           static_assert(M > 16 && M <= 20, "19 derivative columns: 16 + 4 loaded");
           float d0[16], d1[4];
-          tc::tmem_ld16(tbase + lane_base + der_col(i), d0);
-          tc::tmem_ld4(tbase + lane_base + der_col(i) + 16u, d1);
+          tc::tmem_ld16_4_16(tbase + lane_base + der_col(i), tbase + lane_base + der_col(i) + 16u,
+                             tbase + lane_base + face_col(i) + 16u * h, d0, d1, f);
           if (weno_row) {
             float bq = 0.0f;
 #pragma unroll
@@ -812,9 +813,9 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
               cq = fmaf(-w0g, gq, wq);  // w~_q - w~_0 gamma_q / gamma_0
             }
           }
+        } else {
+          tc::tmem_ld16(tbase + lane_base + face_col(i) + 16u * h, f);
         }
-        float f[16];
-        tc::tmem_ld16(tbase + lane_base + face_col(i) + 16u * h, f);
 #pragma unroll
         for (int m = 0; m < 16; ++m) acc[m] = fmaf(cq, f[m], acc[m]);
         tc::fence_before_sync();
