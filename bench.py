@@ -566,6 +566,26 @@ def main():
         for line in open(tfile):
             if line.startswith("traffic_bytes_per_launch"):
                 traffic = float(line.split("=")[1])
+    tensor = None
+    if kern == "recon32" and W.dims == 3 and W.R == 3 and kms > 0:
+        # the tcgen05 contraction's issued work: per tile of 128 cells and variable, 23 k-steps of three
+        # kind::f16 MMAs of 128 x 96 x 16 (every tile counted as running all 23 k-steps: an upper bound, since
+        # all-linear tiles run 8), against the measured dense bf16 peak (fp16 has the same nominal rate)
+        import math
+        # 8 x 4 x 4 tiles of the whole grid (z-slab launches also issue the MMAs of their partly filled tiles)
+        tiles_total = math.ceil(W.n[0] / 8) * math.ceil(W.n[1] / 4) * math.ceil(W.n[2] / 4)
+        mma_flops = tiles_total * 5 * 23 * 3 * (2 * 128 * 96 * 16)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            pass
+        tpeak = peaks.get("bf16_tflops_sustained") or 1700.0
+        issued = mma_flops * 3 * traced / (kms * 1e-3) / 1e12
+        tensor = {"issued_tflops": issued, "peak": tpeak, "frac": issued / tpeak,
+                  "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kind::f16 FP16 has the bf16 rate)",
+                  "note": "MMA flops issued (three FP16 hi/lo products per k-step, every tile 23 k-steps: an upper "
+                          "bound) over the kernel's device time"}
     total_prof = sum(v[1] for v in prof.values())
     kname = {"recon64": "recon64_kernel", "recon32": "recon32_kernel"}[kern]
     if kern == "recon32" and W.dims == 3 and W.R == 3:
@@ -580,6 +600,7 @@ def main():
                 "achieved_incl_gate_tflops": ((flops + gate_flops_per_cell(W.dims) * ncell) * 3 * traced
                                               / (kms * 1e-3) / 1e12) if (path == "gated" and kms > 0) else None,
                 "launches_per_stage": launches_per_stage,
+                "tensor_pipe": tensor,
                 "kernel_share": {k: round(v[1] / total_prof, 4) for k, v in prof.items()} if total_prof else {}}
 
     # ---- the accuracy side of the metric ----
