@@ -3,8 +3,10 @@
 // The same mathematics as recon32.cuh, arranged for the size of this case: S0 has
 // 123 cells, there are 8 stencils with 348 (stencil, cell) pairs, 54 face points
 // and 19 derivative multi-indices, i.e. 25,404 multiply-adds per variable and
-// cell.  Unrolling that with compile-time weights, as the smaller cases do, would
-// give a kernel of ~10^5 instructions, so here
+// cell.  Two kernels: recon33_tc_kernel (the default) runs the contraction on the
+// tcgen05 tensor cores (described at its namespace below); recon33_kernel runs it
+// on the FP32 pipe.  Unrolling the contraction with compile-time weights, as the
+// smaller cases do, would give a kernel of ~10^5 instructions, so in recon33_kernel
 //   * the weights are a float32 row table in global memory, one row of 56 face
 //     values + 20 derivative values (zero padded, float4 aligned) per (stencil,
 //     cell) pair; every thread of a warp reads the same row, so the loads are
@@ -534,7 +536,7 @@ namespace tcg {
 constexpr int KS = 23;                     // k-steps of 16
 constexpr int KT = KS * 16;                // padded K = 368
 constexpr int TCT = 512;                   // threads per CTA: 4 per cell row (a quarter of each k-step)
-constexpr int KPC = 2;                     // MMA k-steps per ring chunk (one CTA barrier per chunk)
+constexpr int KPC = 2;                     // MMA k-steps per ring chunk (one full / free hand-off each)
 constexpr int NB = 2;                      // A ring buffers
 constexpr int NREG = 2;                    // TMEM regions, one stencil's accumulators each
 constexpr int NOUT = 96;                   // MMA columns per k-step: 32 derivative + 64 face values
@@ -898,8 +900,8 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
       for (int m = 0; m < 16; ++m) acc[m] = 16 * h + m < F ? acc[m] * inv_w * cs2[16 * h + m] * sc : 0.0f;
       tc::tmem_st16(tbase + lane_base + park_col(v, h), acc);
     }
-    // one CTA-wide check per tile (nothing between the variables needs a CTA barrier: the ring,
-    // the TMEM regions and the dW slots each have their own hand-offs)
+    // one CTA-wide check per tile (nothing between the variables needs a CTA barrier: the ring and
+    // the TMEM regions have their own hand-offs, and each thread parks and reads back its own dW)
     ok = __syncthreads_and(ok) != 0;
     if (!ok) break;
     // the tail, four threads per cell, on the dW each thread parked itself in tensor memory; the A
@@ -967,7 +969,8 @@ void recon33_tc_fill_image(const double* w, unsigned char* out) {
     wo += tab.len[q] * (F + M);
     ks += (tab.len[q] + 15) / 16 * 16;
   }
-  // weight of output column n (pass 1: derivative n of stencil q; pass 2: face point n) at padded K kk
+  // weight of output column n (kind 1: derivative n of the k-step's stencil; kind 2: face point n) at
+  // padded K kk
   auto weight = [&](int pass, int n, int kk) -> double {
     const int q = km.kq[kk / 16];
     const int jin = kk - kstart[q], len = tab.len[q];
