@@ -837,11 +837,16 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
 #pragma unroll
         for (int jj = 0; jj < KPC; ++jj) {
           if (jj < nj) {
-            float xv[4];
+            // a linear row takes S0 alone and no smoothness indicator: its substencil columns stay zero
+            // (a warp whose rows are all linear skips their gathers)
+            const bool row_needs = active && (weno_row || j0 + jj <= last_kstep(0));
+            float xv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (row_needs) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int o = koff[16 * (j0 + jj) + 4 * h + e];
-              xv[e] = (active && o != kPad) ? ref.delta_scaled(sm, c + o, fs) : 0.0f;
+              for (int e = 0; e < 4; ++e) {
+                const int o = koff[16 * (j0 + jj) + 4 * h + e];
+                if (o != kPad) xv[e] = ref.delta_scaled(sm, c + o, fs);
+              }
             }
             // hi = FP16 rounding of each value (one rounding per pair), lo = FP16 of the remainder
             const __half2 h01 = __floats2half2_rn(xv[0], xv[1]), h23 = __floats2half2_rn(xv[2], xv[3]);
