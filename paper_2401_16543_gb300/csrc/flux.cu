@@ -412,6 +412,14 @@ struct FTile {
   static constexpr int NF0 = (TX + 1) * TY * TZ, NF1 = TX * (TY + 1) * TZ, NF2 = (D == 3) ? TX * TY * (TZ + 1) : 0;
   static constexpr int NF = NF0 + NF1 + NF2;
   __host__ __device__ static constexpr int off(int d) { return d == 0 ? 0 : (d == 1 ? NF0 : NF0 + NF1); }
+  // faces of direction d, and where direction d starts in the warp-padded order
+  // the threads deal them out in
+  __host__ __device__ static constexpr int nfd(int d) { return d == 0 ? NF0 : (d == 1 ? NF1 : NF2); }
+  __host__ __device__ static constexpr int pad(int n) { return (n + 31) / 32 * 32; }
+  __host__ __device__ static constexpr int eoff(int d) {
+    return d == 0 ? 0 : (d == 1 ? pad(NF0) : pad(NF0) + pad(NF1));
+  }
+  static constexpr int NE = pad(NF0) + pad(NF1) + pad(NF2);
   // index of face with local coordinates (x, y, z) in direction d's array
   __device__ static int idx(int d, int x, int y, int z) {
     const int ex = TX + (d == 0), ey = TY + (d == 1);
@@ -420,7 +428,7 @@ struct FTile {
 };
 
 template <int D, int R, typename Real, bool SHADOW>
-__global__ void __launch_bounds__(FTile<D>::THREADS, 5) flux_update_kernel(GridArgs a, const Real* __restrict__ faces,
+__global__ void __launch_bounds__(FTile<D>::THREADS, sizeof(Real) == 8 ? 3 : 5) flux_update_kernel(GridArgs a, const Real* __restrict__ faces,
                                                                         int stage, const double* __restrict__ U0,
                                                                         const double* __restrict__ Us,
                                                                         double* __restrict__ out,
@@ -439,25 +447,31 @@ __global__ void __launch_bounds__(FTile<D>::THREADS, 5) flux_update_kernel(GridA
   const int l[3] = {tid % T::TX, (tid / T::TX) % T::TY, tid / (T::TX * T::TY)};
   const int c[3] = {bx * T::TX + l[0], by * T::TY + l[1], (D == 3) ? a.zc_lo + bz * T::TZ + l[2] : 0};
   const bool active = c[0] < a.n[0] && c[1] < a.n[1] && c[2] < (D == 3 ? a.zc_hi : 1);
-  const int tdim[3] = {T::TX, T::TY, T::TZ};
   const int last[3] = {a.n[0] - 1, a.n[1] - 1, (D == 3 ? a.zc_hi : 1) - 1};
-  if (active) {
+  // Every face flux touching the tile, each once.  The faces are dealt out in
+  // direction blocks padded to whole warps, so a warp works on one direction and
+  // the CTA's threads share the tile's faces evenly (a tile has more faces than
+  // cells: its high faces along each direction).
+  {
     bool ok = true;
+    const int org[3] = {bx * T::TX, by * T::TY, (D == 3) ? a.zc_lo + bz * T::TZ : 0};
+    for (int e = tid; e < T::NE; e += T::THREADS) {
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      Real f[NV];
-      ok &= face_flux_at<D, R, Real>(a, faces, d, c, ncell, f);
-      const int i0 = T::idx(d, l[0], l[1], l[2]);
+      for (int d = 0; d < D; ++d) {
+        const int j = e - T::eoff(d);
+        const int ex = T::TX + (d == 0), ey = T::TY + (d == 1);
+        if (j >= 0 && j < T::nfd(d)) {
+          int fc[3] = {org[0] + j % ex, org[1] + (j / ex) % ey, org[2] + j / (ex * ey)};
+          bool need = true;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sflux[v][i0] = f[v];
-      if (l[d] == tdim[d] - 1 || c[d] == last[d]) {
-        int ch[3] = {c[0], c[1], c[2]}, lh[3] = {l[0], l[1], l[2]};
-        ch[d] += 1;
-        lh[d] += 1;
-        ok &= face_flux_at<D, R, Real>(a, faces, d, ch, ncell, f);
-        const int i1 = T::idx(d, lh[0], lh[1], lh[2]);
+          for (int k = 0; k < 3; ++k) need &= fc[k] <= last[k] + (k == d);
+          if (need) {
+            Real f[NV];
+            ok &= face_flux_at<D, R, Real>(a, faces, d, fc, ncell, f);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sflux[v][i1] = f[v];
+            for (int v = 0; v < NV; ++v) sflux[v][T::off(d) + j] = f[v];
+          }
+        }
       }
     }
     if (!ok) raise_flag(a.status, kFlagNonphysical);
