@@ -118,7 +118,19 @@ def parse():
                     help="time the headline path only (no other paths, e2e or CPU baseline): for profiler runs")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["voronoi2d-1024", "halfsine3d-256", "mixed2d-2048", "mixed3d-64-r3", "mixed3d-512-r3"])
-    return ap.parse_args()
+    ap.add_argument("--crop", type=int, default=None,
+                    help="with --headline-only: run on the corner crop of this edge of the workload's state (the "
+                         "same regions at the same scale, a grid small enough for a profiler capture)")
+    args = ap.parse_args()
+    if args.crop is not None and not args.headline_only:
+        ap.error("--crop needs --headline-only")
+    return args
+
+
+def cropped(W, c):
+    """The corner crop c^d of workload W as a workload of its own."""
+    return Workload(f"{W.name}-crop{c}", W.dims, W.R, [c] * W.dims, W.bc, f"{W.desc}; corner crop {c}^{W.dims}",
+                    lambda dev, crop=None: W.make(dev, crop=c), gate=W.gate, cpu_crop=W.cpu_crop)
 
 
 def dist_setup(args):
@@ -459,6 +471,8 @@ def main():
     import paper_2401_16543_gb300 as pkg
     pkg.load()
     W = _workloads()[args.workload]
+    if args.crop is not None:
+        W = cropped(W, args.crop)
     dev = torch.device("cuda", local)
     t_gen = time.perf_counter()
     U0 = W.make(dev).contiguous()

@@ -140,9 +140,13 @@ size_t kfvm_weights_count(const kfvm_ctx* ctx);
  *                 hi/lo split operands, FP32 accumulation in tensor memory) or
  *                 on the FP32 pipe.  Ignored elsewhere.
  *   "slab_planes" 3D only: process kfvm_step / kfvm_rhs in z-slabs of this many
- *                 planes (at most what the Riemann-state buffer was sized for;
- *                 kfvm_init sizes it to the whole grid up to 8 GiB, else to
- *                 slabs).  Results do not depend on the slab size.
+ *                 planes.  The Riemann-state buffer holds the whole grid's
+ *                 float64 states up to 24 GiB; above that the library picks
+ *                 the slabs itself (as few as the buffer holds, the float32
+ *                 mode's half-size states taking twice the planes), and a
+ *                 slab of S planes needs S + 2 planes of states: a larger
+ *                 value is lowered to fit.  Results do not depend on the slab
+ *                 size.
  *   "timeout_probe" 1: test hook of the bounded device waits: the next
  *                 tensor-core launch waits on a barrier phase nothing completes,
  *                 gives up after a short limit, raises the timeout flag (read by

@@ -191,6 +191,36 @@ kfvm_status check_ready(kfvm_ctx* ctx) {
   return KFVM_OK;
 }
 
+// Bytes of the Riemann-state buffer: 3D grids whose float64 states exceed it are stepped in z-slabs.
+constexpr size_t kFaceBudget = (size_t)24 << 30;
+
+// Bytes the Riemann states of one z-plane take in the current precision: float64 conservative
+// values, or float32 primitive values (a float4 per point plus, in 3D, a float of w).
+size_t face_plane_bytes(const kfvm_ctx* c) {
+  const size_t per_point = c->precision == 64 ? (size_t)c->nv * sizeof(double) : (c->dims == 3 ? 20 : 16);
+  return per_point * c->F * c->n[0] * c->n[1];
+}
+
+// z-planes per slab of a 3D step (= n[2]: one pass over the whole grid).  A slab of S planes
+// reconstructs S + 2 (one on each side for its boundary faces), so the automatic choice takes as
+// few slabs as the buffer allows, makes them even, and rounds S + 2 up to a multiple of the
+// reconstruction's z-tile when the buffer still holds it (no partly empty tiles).
+int slab_planes(const kfvm_ctx* c) {
+  const int nz = c->n[2];
+  if (c->dims != 3) return nz;
+  const long long P = (long long)(c->face_bytes / face_plane_bytes(c));  // >= 3 (see kfvm_init)
+  if (c->slab_user > 0) {
+    if (c->slab_user >= nz && P >= nz) return nz;
+    return (int)(c->slab_user < P - 2 ? c->slab_user : P - 2);
+  }
+  if (P >= nz) return nz;
+  const long long smax = P - 2, ns = (nz + smax - 1) / smax;
+  long long s = (nz + ns - 1) / ns;
+  const int tz = (c->precision == 32 && c->R == 3) ? 4 : 2;
+  const long long sa = (s + 2 + tz - 1) / tz * tz - 2;
+  return (int)(sa <= smax ? sa : s);
+}
+
 }  // namespace
 
 namespace kfvm {
@@ -291,21 +321,18 @@ kfvm_status kfvm_init(kfvm_ctx** out, const kfvm_grid* g, int dims, int radius, 
   if (e == cudaSuccess)
     e = dalloc(&c->d_w32, (dims == 3 && radius == 3) ? recon33_table_floats() : c->wcount);
   if (e == cudaSuccess && dims == 3 && radius == 3) e = cudaMalloc(&c->d_w33tc, recon33_tc_image_bytes());
-  // Riemann-state buffer: the whole grid if it fits in 8 GiB (float64), else 3D z-slabs
-  // of S planes plus one plane on each side (kfvm_step loops over the slabs)
+  // Riemann-state buffer: the whole grid's float64 states if they fit in kFaceBudget, else
+  // kFaceBudget (at least three planes); 3D steps then run in z-slabs (slab_planes below)
   {
-    const size_t plane = (size_t)F * nv * c->n[0] * c->n[1] * sizeof(double);
-    const size_t budget = (size_t)8 << 30;
-    if (dims == 2 || plane * c->n[2] <= budget) {
-      c->slab_planes = c->n[2];
-      c->face_planes = c->n[2];
-    } else {
-      const long long s = (long long)(budget / plane) - 2;
-      c->slab_planes = (int)(s < 1 ? 1 : (s > c->n[2] ? c->n[2] : s));
-      c->face_planes = c->slab_planes + 2;
+    const size_t plane = (size_t)F * nv * c->n[0] * c->n[1];  // float64 values per z-plane
+    size_t count = plane * c->n[2];
+    if (dims == 3 && count * sizeof(double) > kFaceBudget) {
+      count = kFaceBudget / sizeof(double);
+      if (count < 3 * plane) count = 3 * plane;
     }
+    c->face_bytes = count * sizeof(double);
+    if (e == cudaSuccess) e = dalloc((double**)&c->d_faces, count);
   }
-  if (e == cudaSuccess) e = dalloc((double**)&c->d_faces, (size_t)F * nv * c->n[0] * c->n[1] * c->face_planes);
   if (e == cudaSuccess) e = dalloc(&c->d_flux, flux_total);
   if (e == cudaSuccess) e = dalloc(&c->d_stage, nv * nc);
   if (e == cudaSuccess) e = dalloc(&c->d_shadow, nv * nc);
@@ -421,10 +448,9 @@ kfvm_status kfvm_set_option(kfvm_ctx* ctx, const char* key, double v) {
     if (v != 0 && v != 1) return KFVM_ERR_ARG;
     ctx->timeout_probe = (int)v;
   } else if (k == "slab_planes") {
-    // split 3D steps into z-slabs of this many planes (at most what the buffer was sized for)
+    // split 3D steps into z-slabs of this many planes (at most what the buffer holds)
     if (!(v >= 1) || ctx->dims != 3) return KFVM_ERR_ARG;
-    const int limit = ctx->face_planes == ctx->n[2] ? ctx->n[2] : ctx->face_planes - 2;
-    ctx->slab_planes = (int)v < limit ? (int)v : limit;
+    ctx->slab_user = v < ctx->n[2] ? (int)v : ctx->n[2];
   } else if (k == "profile") {
     if (v != 0 && v != 1) return KFVM_ERR_ARG;
     ctx->profile = (int)v;
@@ -479,7 +505,7 @@ namespace {
 kfvm_status stage_pass(kfvm_ctx* ctx, int stage, const double* in, const double* U0, double* out,
                        const float* shadow_in, float* shadow_out, cudaStream_t st) {
   const bool fp32 = ctx->precision == 32;
-  const int nz = ctx->n[2], S = ctx->slab_planes;
+  const int nz = ctx->n[2], S = slab_planes(ctx);
   const bool multi = ctx->dims == 3 && S < nz;
   for (int z0 = 0; z0 < (multi ? nz : 1); z0 += (multi ? S : 1)) {
     const int zc_lo = multi ? z0 : 0, zc_hi = multi ? (z0 + S < nz ? z0 + S : nz) : 0;
@@ -497,7 +523,7 @@ kfvm_status stage_pass(kfvm_ctx* ctx, int stage, const double* in, const double*
 }
 
 kfvm_status ensure_slab_buffers(kfvm_ctx* ctx) {
-  if (!(ctx->dims == 3 && ctx->slab_planes < ctx->n[2])) return KFVM_OK;
+  if (!(ctx->dims == 3 && slab_planes(ctx) < ctx->n[2])) return KFVM_OK;
   const size_t n = (size_t)ctx->nv * ctx->ncell;
   if (!ctx->d_stage2) KFVM_TRY(cudaMalloc(&ctx->d_stage2, sizeof(double) * n));
   if (!ctx->d_shadow2) KFVM_TRY(cudaMalloc(&ctx->d_shadow2, sizeof(float) * n));
@@ -531,7 +557,7 @@ kfvm_status kfvm_step(kfvm_ctx* ctx, double* U, double cfl, double t_remaining, 
   if (s) return s;
   cudaStream_t st = (cudaStream_t)stream;
   const bool fp32 = ctx->precision == 32;
-  const bool multi = ctx->dims == 3 && ctx->slab_planes < ctx->n[2];
+  const bool multi = ctx->dims == 3 && slab_planes(ctx) < ctx->n[2];
   // dt from U (and, in the FP32 mode, the float32 shadow of U for the first stage)
   KFVM_LAUNCH(ctx, kProfMaxRate, st, launch_max_rate(ctx, U, cfl, t_remaining, st));
   // Shu-Osher stages; with slabs no stage writes the state its own reconstruction still reads

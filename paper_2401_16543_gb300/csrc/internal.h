@@ -71,8 +71,8 @@ struct kfvm_ctx {
   double* d_stage = nullptr;     // one intermediate RK state, nv * ncell
   double* d_stage2 = nullptr;    // second intermediate state (only when the step runs in z-slabs)
   float* d_shadow2 = nullptr;    // second float32 shadow (slabs)
-  int slab_planes = 1;           // z-planes per slab; = n[2] for a single slab
-  int face_planes = 1;           // z-planes the Riemann-state buffer can hold
+  size_t face_bytes = 0;         // bytes of the Riemann-state buffer d_faces
+  int slab_user = 0;             // z-planes per slab set by the "slab_planes" option (0: automatic)
   double* d_L = nullptr;         // optional dUdt scratch for kfvm_rhs-style calls
   float* d_shadow = nullptr;     // float32 copy of the state for the FP32 path, nv * ncell
   unsigned char* d_gate_mask = nullptr;  // per cell: 1 = smooth (linear), 0 = WENO
