@@ -103,20 +103,31 @@ struct Ref {
     t = fmaf(-ut[2], sm[3 * SN + o] - uc[3], t);
     return gm1 * t;
   }
-  // delta(o) times a power of two inv_s, the scale folded into the row's last factor (1, 1 / rho~,
-  // gamma - 1): the same bits as delta(o) * inv_s
-  __device__ __forceinline__ float delta_scaled(const float* __restrict__ sm, int o, float fs) const {
-    const float dr = sm[o] - uc[0];
-    if (v == 0) return dr * fs;
-    if (v <= 3) return fmaf(-uv, dr, sm[v * SN + o] - ucv) * fs;
-    float t = fmaf(kin, dr, sm[4 * SN + o] - uc[4]);
-    t = fmaf(-ut[0], sm[SN + o] - uc[1], t);
-    t = fmaf(-ut[1], sm[2 * SN + o] - uc[2], t);
-    t = fmaf(-ut[2], sm[3 * SN + o] - uc[3], t);
-    return t * fs;
-  }
   __device__ __forceinline__ float fold(float inv_s) const {
     return v == 0 ? inv_s : (v <= 3 ? irt * inv_s : gm1 * inv_s);
+  }
+  // delta(o) times a power of two inv_s of the variable V (= v, known at compile time) at the four tile
+  // offsets o of cell cc, the scale folded into the row's last factor (fs = fold(inv_s): the same
+  // bits as delta(o) * inv_s)
+  template <int V>
+  __device__ __forceinline__ void deltas4(const float* __restrict__ sm, int cc, int4 o, float fs,
+                                          float (&x)[4]) const {
+    const int oo[4] = {cc + o.x, cc + o.y, cc + o.z, cc + o.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float dr = sm[oo[e]] - uc[0];
+      if constexpr (V == 0) {
+        x[e] = dr * fs;
+      } else if constexpr (V <= 3) {
+        x[e] = fmaf(-ut[V - 1], dr, sm[V * SN + oo[e]] - uc[V]) * fs;
+      } else {
+        float t = fmaf(kin, dr, sm[4 * SN + oo[e]] - uc[4]);
+        t = fmaf(-ut[0], sm[SN + oo[e]] - uc[1], t);
+        t = fmaf(-ut[1], sm[2 * SN + oo[e]] - uc[2], t);
+        t = fmaf(-ut[2], sm[3 * SN + oo[e]] - uc[3], t);
+        x[e] = t * fs;
+      }
+    }
   }
 };
 
@@ -563,9 +574,9 @@ struct KMap {
   int kq[KS];       // stencil of each k-step
   int first[KS];    // 1 on the first k-step of a stencil
   int last_of[NQ];  // last k-step of each stencil
-  int off[KT];      // tile offset of each padded K column; kPad for padding
+  int off[KT];      // tile offset of each padded K column (0 for padding: the row's own cell, whose
+                    // delta is exactly zero; the padding's B rows are zero too)
 };
-constexpr int kPad = 1 << 28;
 
 constexpr KMap make_kmap() {
   KMap m{};
@@ -582,7 +593,7 @@ constexpr KMap make_kmap() {
         const int l = G::tab.idx[q][j];
         m.off[kk] = G::tab.off[l][0] + T::SX * (G::tab.off[l][1] + T::SY * G::tab.off[l][2]);
       } else {
-        m.off[kk] = kPad;
+        m.off[kk] = 0;
       }
     }
     m.last_of[q] = kk / 16 - 1;
@@ -842,10 +853,13 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
             const bool row_needs = active && (weno_row || j0 + jj <= last_kstep(0));
             float xv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             if (row_needs) {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const int o = koff[16 * (j0 + jj) + 4 * h + e];
-                if (o != kPad) xv[e] = ref.delta_scaled(sm, c + o, fs);
+              const int4 o4 = *reinterpret_cast<const int4*>(koff + 16 * (j0 + jj) + 4 * h);
+              switch (v) {  // uniform: the variable's arithmetic chosen once per k-step
+                case 0: ref.deltas4<0>(sm, c, o4, fs, xv); break;
+                case 1: ref.deltas4<1>(sm, c, o4, fs, xv); break;
+                case 2: ref.deltas4<2>(sm, c, o4, fs, xv); break;
+                case 3: ref.deltas4<3>(sm, c, o4, fs, xv); break;
+                default: ref.deltas4<4>(sm, c, o4, fs, xv); break;
               }
             }
             // hi = FP16 rounding of each value (one rounding per pair), lo = FP16 of the remainder
@@ -870,7 +884,13 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
         if (tid == 0) {
           if (!tc::mbar_wait(chunk_full + buf, use & 1u, WAIT_LIMIT)) ok = false;
           tc::fence_after_sync();
-          for (int jj = 0; jj < nj; ++jj) {
+          // descriptors: the chunk's and the weight image's base, plus the k-step's offset (>> 4, the
+          // address field's unit; every address stays below 2^18)
+          const uint64_t abase = tc::smem_desc(a_addr + buf * A_BUF, 128, 256);
+          const uint64_t bbase = tc::smem_desc(b_addr, 128, 256);
+#pragma unroll
+          for (int jj = 0; jj < KPC; ++jj) {
+            if (jj >= nj) break;
             const int j = j0 + jj, q = kstep_stencil(j), i = q % NREG;
             const bool first = (kFirst >> j) & 1u;
             if (first) {
@@ -884,10 +904,8 @@ __global__ void __launch_bounds__(TCT, 1) recon33_tc_kernel(GridArgs a, int mode
             // derivative and face columns of stencil q in one N = 96 MMA per product (all-linear
             // tiles compute the derivative columns too and ignore them)
             const uint32_t acc0 = first ? 0u : 1u;
-            const uint32_t ab = a_addr + buf * A_BUF + jj * A_KS;
-            const uint64_t ahi = tc::smem_desc(ab, 128, 256), alo = tc::smem_desc(ab + A_KS / 2, 128, 256);
-            const uint32_t bh = b_addr + j * BB_BLOCK;
-            const uint64_t bhi = tc::smem_desc(bh, 128, 256), blo = tc::smem_desc(bh + BB_BLOCK / 2, 128, 256);
+            const uint64_t ahi = abase + (uint64_t)((jj * A_KS) >> 4), alo = ahi + (uint64_t)((A_KS / 2) >> 4);
+            const uint64_t bhi = bbase + (uint64_t)((j * BB_BLOCK) >> 4), blo = bhi + (uint64_t)((BB_BLOCK / 2) >> 4);
             tc::mma_f16(tbase + der_col(i), ahi, bhi, id96, acc0);
             tc::mma_f16(tbase + der_col(i), ahi, blo, id96, 1u);
             tc::mma_f16(tbase + der_col(i), alo, bhi, id96, 1u);
