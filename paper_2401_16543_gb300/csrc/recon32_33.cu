@@ -523,7 +523,7 @@ __device__ __forceinline__ void write_states_split(const GridArgs& a, const floa
 // Each chunk of A is built once per (tile, variable) and feeds one GEMM per product
 // with N = 96 columns: the 32 derivative columns of its stencil (Eq. 23 rows, 19 used)
 // and the 64 face columns (Eq. 18 rows, 54 used), one B block per k-step.  A stencil's
-// accumulators occupy one of four TMEM regions (columns 128 i ... 128 i + 95); the stencils
+// accumulators occupy one of two TMEM regions (columns 128 i ... 128 i + 95); the stencils
 // are consumed in order as soon as their MMAs complete: beta_q (Eq. 22) -> the
 // unnormalised WENO weight w~_q = gamma_q / (beta'^2 + eps') (Eq. 24, beta' = beta / s^2,
 // eps' = eps / s^4, the same weights as gamma_q / (beta^2 + eps) after normalisation) ->
