@@ -207,7 +207,35 @@ __device__ __forceinline__ bool riemann64(const double* uL, const double* uR, in
   return true;
 }
 
-template <int D>
+// Reciprocal and square root of the FP32 solver.  FAST: single PTX instructions, rcp.approx.f32 (at
+// most 1 ulp) and sqrt.approx.f32 (relative error ~2^-23), instead of the IEEE-rounded __frcp_rn /
+// sqrtf (a few instructions each and a slow path); the flux/update kernel is partly issue-bound (five
+// square roots and four reciprocals per Riemann solve), 2D 1024^2: 0.077 -> 0.069 ms per stage.  Used
+// at radius 2 only: the radius-3 linear reconstructions amplify high-wavenumber perturbations weakly
+// (a von Neumann symbol with max Re(lambda) dx > 0), and the extra rounding raised the 3D radius-3
+// gated path's L1 error on the 32^3 sine translation from ~1.08 to 1.21 times FP64 WENO-AO's.
+template <bool FAST>
+__device__ __forceinline__ float rcp32(float x) {
+  if constexpr (FAST) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  } else {
+    return __frcp_rn(x);
+  }
+}
+template <bool FAST>
+__device__ __forceinline__ float sqrt32(float x) {
+  if constexpr (FAST) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  } else {
+    return sqrtf(x);
+  }
+}
+
+template <int D, bool FAST>
 __device__ __forceinline__ bool riemann32(const float* wL, const float* wR, int dir, float gamma, int solver,
                                           float* f) {
   constexpr int NV = D + 2;
@@ -224,11 +252,11 @@ __device__ __forceinline__ bool riemann32(const float* wL, const float* wR, int 
     v2L = fmaf(wL[1 + k], wL[1 + k], v2L);
     v2R = fmaf(wR[1 + k], wR[1 + k], v2R);
   }
-  const float igm1 = __frcp_rn(gm1);
+  const float igm1 = rcp32<FAST>(gm1);
   const float EL = fmaf(pL, igm1, 0.5f * rL * v2L), ER = fmaf(pR, igm1, 0.5f * rR * v2R);
-  const float irL = __frcp_rn(rL), irR = __frcp_rn(rR);
-  const float cL = sqrtf(gamma * pL * irL), cR = sqrtf(gamma * pR * irR);
-  const float sL = sqrtf(rL), sR = sqrtf(rR), isum = __frcp_rn(sL + sR);
+  const float irL = rcp32<FAST>(rL), irR = rcp32<FAST>(rR);
+  const float cL = sqrt32<FAST>(gamma * pL * irL), cR = sqrt32<FAST>(gamma * pR * irR);
+  const float sL = sqrt32<FAST>(rL), sR = sqrt32<FAST>(rR), isum = rcp32<FAST>(sL + sR);
   float ut2 = 0.0f, utn = 0.0f;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -239,7 +267,7 @@ __device__ __forceinline__ bool riemann32(const float* wL, const float* wR, int 
   const float HL = (EL + pL) * irL, HR = (ER + pR) * irR;
   const float Ht = (sL * HL + sR * HR) * isum;
   const float ct2 = gm1 * (Ht - 0.5f * ut2);
-  const float ct = sqrtf(ct2 > 0.0f ? ct2 : 0.0f);
+  const float ct = sqrt32<FAST>(ct2 > 0.0f ? ct2 : 0.0f);
   const float unL = wL[1 + dir], unR = wR[1 + dir];
   const float SL = fminf(unL - cL, utn - ct), SR = fmaxf(unR + cR, utn + ct);
   float UL[NV], UR[NV], FL[NV], FR[NV];
@@ -272,7 +300,7 @@ __device__ __forceinline__ bool riemann32(const float* wL, const float* wR, int 
     return true;
   }
   if (solver == 1) {
-    const float idn = __frcp_rn(SR - SL);
+    const float idn = rcp32<FAST>(SR - SL);
 #pragma unroll
     for (int v = 0; v < NV; ++v) f[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) * idn;
     return true;
@@ -365,7 +393,7 @@ __device__ __forceinline__ bool face_flux_at(const GridArgs& a, const Real* __re
     if constexpr (sizeof(Real) == 8)
       ok &= riemann64<D>(uL, uR, dir, a.gamma, a.riemann, fl);
     else
-      ok &= riemann32<D>(uL, uR, dir, (float)a.gamma, a.riemann, fl);
+      ok &= riemann32<D, R == 2>(uL, uR, dir, (float)a.gamma, a.riemann, fl);
     const double wt = (R == 2 ? w2[t % R] : w3[t % R]) * (D == 3 ? (R == 2 ? w2[t / R] : w3[t / R]) : 1.0);
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] += Real(wt) * fl[v];
