@@ -428,8 +428,9 @@ __global__ void __launch_bounds__(kBlock) face_flux_kernel(GridArgs a, FluxLayou
 // ---------------------------------------------------------------------------
 // Fused flux divergence and SSP-RK3 stage (the hot-path version): a CTA owns a
 // tile of cells, computes every face flux touching the tile exactly once into
-// shared memory (the tile's high faces by its last cells), then each thread
-// forms L = -sum_d (F_hi - F_lo)/Delta_d for its cell and the stage update.
+// shared memory (the faces, the tile's high faces included, dealt out evenly to
+// its threads), then each thread forms L = -sum_d (F_hi - F_lo)/Delta_d for its
+// cell and the stage update.
 // Float64 faces: L and the update in float64 (the plain path).  Float32 faces:
 // L in float32, the stage combination accumulated in float64.
 // ---------------------------------------------------------------------------
