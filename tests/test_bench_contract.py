@@ -67,3 +67,13 @@ def test_reference_arm_prints_one_json_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["higher_is_better"] is True and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_crop_is_the_corner_of_the_workload_and_needs_headline_only():
+    W = bench._workloads()["mixed3d-64-r3"]
+    C = bench.cropped(W, 16)
+    assert C.n == [16, 16, 16] and C.ncell == 16 ** 3 and C.R == W.R and C.gate == W.gate
+    assert torch.equal(C.make("cpu"), W.make("cpu")[:, :16, :16, :16])
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--crop", "16"], capture_output=True,
+                       text=True, cwd=ROOT)
+    assert r.returncode != 0 and "--crop needs --headline-only" in r.stderr
