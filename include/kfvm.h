@@ -124,8 +124,10 @@ size_t kfvm_weights_count(const kfvm_ctx* ctx);
  *                 Phi = L and Phi^{-1} = R from the eigenvectors of that
  *                 direction's flux Jacobian at the central cell average, and
  *                 the weights recomputed per direction for its two faces).
- *                 Characteristic variables run on the FP64 path only: in the
- *                 FP32 mode the hot-path calls return KFVM_ERR_STATE.
+ *                 Characteristic variables run on the FP64 path and on the
+ *                 FP32 path in 2D and in 3D at radius 2; with dims = 3,
+ *                 radius 3 in the FP32 mode the hot-path calls return
+ *                 KFVM_ERR_STATE.
  *   "riemann"     0 HLLC (default), 1 HLL; Batten wave speeds (Sec. 5.4).
  *   "positivity"  1 (default) apply the positivity-preserving limiter of
  *                 Sec. 4 to the Riemann states; 0 off.
