@@ -81,7 +81,9 @@ typedef struct kfvm_ctx kfvm_ctx;
  * Sec. 5.1) and ratio of specific heats gamma.  Enumerates S0 and its 2*dims+1
  * substencils (Sec. 3.1), picks each polynomial degree as the largest that
  * keeps the cell-average monomial matrix unisolvent (Sec. 2.1, exact rank over
- * the integers mod two 61-bit primes), and allocates the device buffers.
+ * the integers mod two 61-bit primes), and allocates the device buffers (the
+ * Riemann-state buffer holds the whole grid's float64 states, in 3D at most
+ * 24 GiB: larger grids are stepped in z-slabs, see "slab_planes").
  * Requires an exactly uniform spacing per axis; cells may be non-square.
  * Errors: KFVM_ERR_ARG (null out/grid, dims/R outside {2,3}, n < 1,
  * hi <= lo, ell <= 0, gamma <= 1, mixed periodic sides), KFVM_ERR_CUDA,
