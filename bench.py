@@ -586,7 +586,8 @@ def main():
         # kind::f16 MMAs of 128 x 96 x 16 (every tile counted as running all 23 k-steps: an upper bound, since
         # all-linear tiles run 8), against the measured dense bf16 peak (fp16 has the same nominal rate)
         import math
-        # 8 x 4 x 4 tiles of the whole grid (z-slab launches also issue the MMAs of their partly filled tiles)
+        # 8 x 4 x 4 tiles of the whole grid (z-slab launches also reconstruct each slab's two boundary planes,
+        # 2.3% more tiles at 512^3, not counted here)
         tiles_total = math.ceil(W.n[0] / 8) * math.ceil(W.n[1] / 4) * math.ceil(W.n[2] / 4)
         mma_flops = tiles_total * 5 * 23 * 3 * (2 * 128 * 96 * 16)
         peaks = {}
@@ -598,8 +599,9 @@ def main():
         issued = mma_flops * 3 * traced / (kms * 1e-3) / 1e12
         tensor = {"issued_tflops": issued, "peak": tpeak, "frac": issued / tpeak,
                   "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kind::f16 FP16 has the bf16 rate)",
-                  "note": "MMA flops issued (three FP16 hi/lo products per k-step, every tile 23 k-steps: an upper "
-                          "bound) over the kernel's device time"}
+                  "note": "MMA flops issued for the grid's own tiles (three FP16 hi/lo products per k-step, every tile "
+                          "counted at 23 k-steps although all-linear tiles run 8; the z-slabs' extra boundary-plane "
+                          "tiles not counted) over the kernel's device time"}
     total_prof = sum(v[1] for v in prof.values())
     kname = {"recon64": "recon64_kernel", "recon32": "recon32_kernel"}[kern]
     if kern == "recon32" and W.dims == 3 and W.R == 3:
